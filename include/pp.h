@@ -1,0 +1,170 @@
+/*
+ * pp.h -- C ABI of the GB300 window solver for the second-order polarization
+ * propagator (arXiv 2512.09811).
+ *
+ * What is computed
+ *   The response matrix of Sec. 2.2, Eq. (m_eigen):
+ *       [A B; B A] (X; Y) = omega [S 0; 0 -S] (X; Y)
+ *   over the particle-hole manifold {a^+ i, i^+ a} with the MP2 ground state,
+ *   to zeroth, first or second order in the fluctuation potential W_N:
+ *     S = 1 + S(2),              S(2)_ia,jb = d_ab rho_oo[i,j] - d_ij rho_vv[a,b]
+ *     A = A(0) + A(1) + A(2),    A(0) = (e_a - e_i) d_ij d_ab,  A(1) = <aj||ib>
+ *     B = B(1) + B(2),           B(1) = <ab||ij>
+ *   (Eqs. s(2), a(0)-a(2), b(0)-b(2); matrix elements are the symmetrised
+ *   double commutators of Eq. (mkk_so) with the normalised MP2 state).  Two-
+ *   electron integrals are density fitted: (pq|rs) = sum_Q B[Q,p,q] B[Q,r,s].
+ *   Interior roots in a frequency window are found with the inverse-Krylov /
+ *   weighted-Jacobi / folded-spectrum method of Sec. 2.5; oscillator strengths
+ *   use the zeroth-order property vector F = mu (Eq. pp_adc).
+ *
+ * Conventions
+ *   Indices are spin orbitals, occupied first.  An "ov block" is a row-major
+ *   [nocc][nvir] array of doubles (element (i,a) at i*nvir + a).  A
+ *   supervector is [2][nocc][nvir]: the X block followed by the Y block.
+ *   Arrays of supervectors are [nvec][2][nocc][nvir], contiguous.
+ *
+ * Ownership
+ *   pp_create copies every input; the caller keeps its buffers.  Output
+ *   buffers are caller-allocated.  The context owns all device memory and
+ *   pp_destroy frees it.  Host pointers may be pageable or pinned.
+ *
+ * Errors
+ *   Every call returns a pp_status; no exception crosses the ABI.  On error
+ *   pp_last_error(ctx) holds a one-line message (ctx may be NULL for errors of
+ *   pp_create, in which case pp_last_error(NULL) returns the last create error
+ *   of the calling thread).
+ *
+ * Threading
+ *   A context is not thread-safe; use one context per host thread, or guard it.
+ *   All device work of a context is issued on one CUDA stream (opt->cuda_stream,
+ *   or a stream the context creates); calls return after that stream is idle
+ *   unless stated otherwise.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_ctx pp_ctx;
+
+typedef enum {
+  PP_OK = 0,
+  PP_EINVAL = 1,      /* bad argument: size, NULL pointer, non-finite input, e_occ >= e_vir */
+  PP_ENOMEM = 2,      /* device or host allocation failed */
+  PP_ECUDA = 3,       /* a CUDA runtime call failed; see pp_last_error */
+  PP_ENOTCONV = 4,    /* solver hit max_iter; best estimates are written */
+  PP_ETIMEOUT = 5,    /* a bounded device wait ran out */
+  PP_EMETRIC = 6,     /* S is not positive definite */
+  PP_EUNSTABLE = 7    /* complex RPA roots (A - B not positive) */
+} pp_status;
+
+typedef enum {
+  PP_FP64 = 0,   /* every contraction in FP64 (the plain form) */
+  PP_BF16 = 2,   /* amplitude contractions on BF16 tensor cores (tcgen05) with FP32
+                    accumulation, the other contractions in FP32; Krylov basis, projected
+                    problem, fold centres and residuals stay FP64 */
+  PP_BF16X3 = 3  /* as PP_BF16 with every tensor-core operand split into a BF16 pair
+                    (hi + lo, three products): FP32-level products, used to refine */
+} pp_precision;
+
+typedef struct {
+  int prec;            /* pp_precision */
+  int order;           /* 0, 1 or 2 */
+  int block;           /* trial vectors per window per iteration (default 8) */
+  int m_max;           /* subspace size before a thick restart (default 96, <= 112) */
+  int max_iter;        /* outer iterations per window (default 200) */
+  double res_tol;      /* convergence: |M x - theta Sigma x| / |x^T Sigma x| (default 1e-7) */
+  double jacobi_floor; /* |D_p| >= jacobi_floor in the Jacobi splitting (default 1e-3 Ha) */
+  int select;          /* 0: k lowest roots in [omega0, omega0+delta]; 1: k nearest omega0 */
+  int refine;          /* PP_BF16 only: split-precision refinement steps (default on) */
+  uint64_t seed;       /* reserved for random initial vectors */
+  void *cuda_stream;   /* cudaStream_t to use, or NULL to create one */
+} pp_options;
+
+/* Fill *opt with the defaults above. */
+void pp_default_options(pp_options *opt);
+
+/*
+ * Create a context for one dot (Sec. 2.2 inputs; density fitting as in Sec. 3).
+ *   eps   [nocc+nvir]            orbital energies, occupied first, host; need
+ *                                max(eps_occ) < min(eps_vir) and finite values
+ *   B     [naux][n][n], n = nocc+nvir, host; B_dtype 0 = double, 1 = float;
+ *         symmetric in the last two indices (only the blocks oo, ov, vv are read)
+ *   mu    [3][nocc][nvir]        dipole integrals, host (may be NULL: no oscillator strengths)
+ * Computes the per-dot intermediates (MP2 densities and the 3-index ring
+ * intermediate, the Jacobi diagonal) on the device.  Returns PP_EMETRIC if the
+ * diagonal of S is not positive.
+ */
+pp_status pp_create(int nocc, int nvir, int naux, const double *eps, const void *B, int B_dtype,
+                    const double *mu, const pp_options *opt, pp_ctx **out);
+
+/*
+ * sigma = M z and (if metric != NULL) metric = Sigma z for nvec supervectors
+ * (the matrix-free product of the abstract and Sec. 2.5.2).
+ *   Z, sigma, metric: [nvec][2][nocc][nvir] doubles; host pointers if
+ *   on_device == 0, device pointers (of the context's device) if on_device == 1.
+ * prec selects the arithmetic: PP_FP64 or PP_BF16 (tensor cores, FP32 accumulation).
+ */
+pp_status pp_sigma(pp_ctx *ctx, int nvec, const double *Z, double *sigma, double *metric,
+                   int prec, int on_device);
+
+/*
+ * diag(A) and diag(S), each [nocc][nvir] host doubles: the Jacobi splitting D
+ * of Sec. 2.5.2 (D = diag(M) - omega diag(Sigma)).
+ */
+pp_status pp_diagonal(pp_ctx *ctx, double *diagA, double *diagS);
+
+/*
+ * Roots of Eq. (m_eigen) inside one window (Sec. 2.5: weighted-Jacobi inverse
+ * Krylov basis, folded-spectrum Rayleigh-Ritz on (M - omega Sigma)^2).
+ *   select 0 (options): the k lowest roots in [omega0, omega0 + delta];
+ *   select 1:           the k roots nearest omega0 (delta ignored).
+ *   omega[k], osc[k], resid[k]: host outputs, ascending omega; osc is 0 if mu was NULL.
+ *   vecs: NULL or host [k][2][nocc][nvir], normalised X^T S X - Y^T S Y = 1.
+ *   *nfound: number of roots written (< k if the window holds fewer).
+ * Returns PP_ENOTCONV (with best estimates written) if max_iter is reached.
+ */
+pp_status pp_solve_window(pp_ctx *ctx, double omega0, double delta, int k, double *omega,
+                          double *osc, double *resid, double *vecs, int *nfound);
+
+/*
+ * Several windows of one dot solved together: all windows' trial blocks go
+ * through one sigma batch per iteration.  Outputs are concatenated per window
+ * at offsets off[w] = sum_{u<w} k[u]; nfound[nwin].
+ */
+pp_status pp_solve_windows(pp_ctx *ctx, int nwin, const double *omega0, const double *delta,
+                           const int *k, double *omega, double *osc, double *resid, int *nfound);
+
+/* Statistics of the last solve: outer iterations, sigma supervectors applied,
+   milliseconds spent in sigma and in the whole solve. */
+pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vectors,
+                        double *sigma_ms, double *solve_ms);
+
+/*
+ * Launch timing of the two tensor-core kernels (a profiling aid for the
+ * roofline of the dominant contraction).  pp_profile(ctx, 1) resets the
+ * counters and records CUDA events around every later launch on the context's
+ * stream; pp_profile(ctx, 0) stops recording.  pp_profile_read returns, for
+ * kernel id 0 (the amplitude contraction GEMM, Eq. (b(2)) ladder and ring
+ * parts) or id 1 (the amplitude slab generator, MP2 t of Sec. 2.2), the number
+ * of launches, their summed device milliseconds and their algorithmic FLOPs
+ * (2 M N K per tensor-core product; K excludes the zero padding).
+ */
+pp_status pp_profile(pp_ctx *ctx, int enable);
+pp_status pp_profile_read(pp_ctx *ctx, int id, long long *launches, double *ms, double *flops);
+
+/* Release everything the context owns.  NULL-safe. */
+void pp_destroy(pp_ctx *ctx);
+
+/* One-line description of the last error on ctx (or of the last failed pp_create). */
+const char *pp_last_error(const pp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PP_H */

@@ -1,0 +1,286 @@
+"""Python binding of the GB300 polarization-propagator window solver.
+
+Thin ctypes marshalling over the C ABI in ``include/pp.h``: every function
+here has the C name, converts arguments, calls the library and turns a
+non-zero status into ``PPError``.  All arithmetic happens in the CUDA
+library; if it is not built, ``load()`` raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpp_gb300.so")
+
+PP_OK, PP_EINVAL, PP_ENOMEM, PP_ECUDA, PP_ENOTCONV, PP_ETIMEOUT, PP_EMETRIC, PP_EUNSTABLE = range(8)
+PP_FP64, PP_BF16, PP_BF16X3 = 0, 2, 3
+STATUS_NAMES = {
+    PP_OK: "PP_OK", PP_EINVAL: "PP_EINVAL", PP_ENOMEM: "PP_ENOMEM", PP_ECUDA: "PP_ECUDA",
+    PP_ENOTCONV: "PP_ENOTCONV", PP_ETIMEOUT: "PP_ETIMEOUT", PP_EMETRIC: "PP_EMETRIC",
+    PP_EUNSTABLE: "PP_EUNSTABLE",
+}
+
+# every symbol declared in include/pp.h
+EXPORTS = (
+    "pp_default_options", "pp_create", "pp_sigma", "pp_diagonal", "pp_solve_window",
+    "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_destroy", "pp_last_error",
+)
+
+
+class pp_options(C.Structure):
+    _fields_ = [
+        ("prec", C.c_int), ("order", C.c_int), ("block", C.c_int), ("m_max", C.c_int),
+        ("max_iter", C.c_int), ("res_tol", C.c_double), ("jacobi_floor", C.c_double),
+        ("select", C.c_int), ("refine", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+_dp = C.POINTER(C.c_double)
+
+
+def load(path: str | None = None):
+    """Load the built library (``__graft_entry__.build()`` or ``_build.py`` makes it)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run paper_2512_09811_gb300._build)")
+        lib = C.CDLL(p)
+        vp = C.c_void_p
+        lib.pp_default_options.argtypes = [C.POINTER(pp_options)]
+        lib.pp_default_options.restype = None
+        lib.pp_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, vp, C.c_int, _dp,
+                                  C.POINTER(pp_options), C.POINTER(vp)]
+        lib.pp_create.restype = C.c_int
+        lib.pp_sigma.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int]
+        lib.pp_sigma.restype = C.c_int
+        lib.pp_diagonal.argtypes = [vp, _dp, _dp]
+        lib.pp_diagonal.restype = C.c_int
+        lib.pp_solve_window.argtypes = [vp, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, vp,
+                                        C.POINTER(C.c_int)]
+        lib.pp_solve_window.restype = C.c_int
+        lib.pp_solve_windows.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int), _dp, _dp, _dp,
+                                         C.POINTER(C.c_int)]
+        lib.pp_solve_windows.restype = C.c_int
+        lib.pp_last_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.pp_last_stats.restype = C.c_int
+        lib.pp_profile.argtypes = [vp, C.c_int]
+        lib.pp_profile.restype = C.c_int
+        lib.pp_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]
+        lib.pp_profile_read.restype = C.c_int
+        lib.pp_destroy.argtypes = [vp]
+        lib.pp_destroy.restype = None
+        lib.pp_last_error.argtypes = [vp]
+        lib.pp_last_error.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def pp_default_options(**kw) -> pp_options:
+    lib = load()
+    opt = pp_options()
+    lib.pp_default_options(C.byref(opt))
+    for k, v in kw.items():
+        if not hasattr(opt, k):
+            raise KeyError(k)
+        setattr(opt, k, v)
+    return opt
+
+
+def _check(st: int, ctx=None):
+    if st not in (PP_OK,):
+        msg = load().pp_last_error(ctx).decode(errors="replace")
+        raise PPError(st, msg)
+
+
+def pp_create(nocc: int, nvir: int, naux: int, eps, B, mu=None, opt: pp_options | None = None):
+    """Returns an opaque context handle (int).  B may be float64 or float32 [naux, n, n]."""
+    lib = load()
+    eps = _f64(eps)
+    B = np.ascontiguousarray(B)
+    if B.dtype == np.float64:
+        bdt = 0
+    elif B.dtype == np.float32:
+        bdt = 1
+    else:
+        B = _f64(B)
+        bdt = 0
+    mu_a = _f64(mu) if mu is not None else None
+    if opt is None:
+        opt = pp_default_options()
+    out = C.c_void_p()
+    st = lib.pp_create(nocc, nvir, naux, _ptr(eps), B.ctypes.data_as(C.c_void_p), bdt,
+                       _ptr(mu_a) if mu_a is not None else None, C.byref(opt), C.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def pp_sigma(ctx, Z, prec: int = PP_FP64, metric: bool = False):
+    """sigma = M z (and Sigma z) for Z[nvec, 2, nocc, nvir].
+
+    Z may be a numpy array (host path) or a CUDA torch tensor of float64
+    (device path: the library reads and writes device memory directly).
+    """
+    lib = load()
+    if hasattr(Z, "is_cuda") and Z.is_cuda:
+        import torch
+
+        Zc = Z.contiguous()
+        if Zc.dtype != torch.float64:
+            raise TypeError("device Z must be float64")
+        sig = torch.empty_like(Zc)
+        met = torch.empty_like(Zc) if metric else None
+        st = lib.pp_sigma(ctx, Zc.shape[0], Zc.data_ptr(), sig.data_ptr(),
+                          met.data_ptr() if metric else None, prec, 1)
+        _check(st, ctx)
+        return (sig, met) if metric else sig
+    Zh = _f64(Z)
+    sig = np.empty_like(Zh)
+    met = np.empty_like(Zh) if metric else None
+    st = lib.pp_sigma(ctx, Zh.shape[0], Zh.ctypes.data, sig.ctypes.data,
+                      met.ctypes.data if metric else None, prec, 0)
+    _check(st, ctx)
+    return (sig, met) if metric else sig
+
+
+def pp_diagonal(ctx, nocc: int, nvir: int):
+    lib = load()
+    dA = np.empty((nocc, nvir))
+    dS = np.empty((nocc, nvir))
+    _check(lib.pp_diagonal(ctx, _ptr(dA), _ptr(dS)), ctx)
+    return dA, dS
+
+
+def pp_solve_window(ctx, omega0: float, delta: float, k: int, nocc: int = 0, nvir: int = 0,
+                    want_vectors: bool = False, allow_notconv: bool = False):
+    lib = load()
+    om = np.zeros(k)
+    osc = np.zeros(k)
+    res = np.zeros(k)
+    nf = C.c_int(0)
+    vecs = np.zeros((k, 2, nocc, nvir)) if want_vectors else None
+    st = lib.pp_solve_window(ctx, float(omega0), float(delta), int(k), _ptr(om), _ptr(osc), _ptr(res),
+                             vecs.ctypes.data if want_vectors else None, C.byref(nf))
+    if not (allow_notconv and st == PP_ENOTCONV):
+        _check(st, ctx)
+    n = nf.value
+    out = dict(omega=om[:n], osc=osc[:n], resid=res[:n], status=st)
+    if want_vectors:
+        out["vectors"] = vecs[:n]
+    return out
+
+
+def pp_solve_windows(ctx, omega0, delta, k, allow_notconv: bool = False):
+    lib = load()
+    omega0 = _f64(omega0)
+    delta = _f64(delta)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    nwin = omega0.size
+    tot = int(kk.sum())
+    om = np.zeros(tot)
+    osc = np.zeros(tot)
+    res = np.zeros(tot)
+    nf = np.zeros(nwin, dtype=np.int32)
+    st = lib.pp_solve_windows(ctx, nwin, _ptr(omega0), _ptr(delta), kk.ctypes.data_as(C.POINTER(C.c_int)),
+                              _ptr(om), _ptr(osc), _ptr(res), nf.ctypes.data_as(C.POINTER(C.c_int)))
+    if not (allow_notconv and st == PP_ENOTCONV):
+        _check(st, ctx)
+    out = []
+    off = 0
+    for w in range(nwin):
+        n = int(nf[w])
+        out.append(dict(omega=om[off:off + n], osc=osc[off:off + n], resid=res[off:off + n]))
+        off += int(kk[w])
+    return out, st
+
+
+def pp_last_stats(ctx):
+    lib = load()
+    it = C.c_int()
+    nv = C.c_longlong()
+    sms = C.c_double()
+    tms = C.c_double()
+    _check(lib.pp_last_stats(ctx, C.byref(it), C.byref(nv), C.byref(sms), C.byref(tms)), ctx)
+    return dict(iterations=it.value, sigma_vectors=nv.value, sigma_ms=sms.value, solve_ms=tms.value)
+
+
+def pp_profile(ctx, enable: bool):
+    _check(load().pp_profile(ctx, 1 if enable else 0), ctx)
+
+
+def pp_profile_read(ctx, kernel_id: int):
+    lib = load()
+    n = C.c_longlong()
+    ms = C.c_double()
+    fl = C.c_double()
+    _check(lib.pp_profile_read(ctx, int(kernel_id), C.byref(n), C.byref(ms), C.byref(fl)), ctx)
+    return dict(launches=n.value, ms=ms.value, flops=fl.value)
+
+
+def pp_destroy(ctx):
+    if ctx:
+        load().pp_destroy(ctx)
+
+
+def pp_last_error(ctx=None) -> str:
+    return load().pp_last_error(ctx).decode(errors="replace")
+
+
+class Dot:
+    """Owning wrapper: one context per synthetic dot."""
+
+    def __init__(self, inp, **opts):
+        self.nocc, self.nvir, self.naux = inp.nocc, inp.nvir, inp.naux
+        self.opt = pp_default_options(**opts)
+        self.ctx = pp_create(inp.nocc, inp.nvir, inp.naux, inp.eps, inp.B, inp.mu, self.opt)
+
+    def sigma(self, Z, prec=PP_FP64, metric=False):
+        return pp_sigma(self.ctx, Z, prec, metric)
+
+    def diagonal(self):
+        return pp_diagonal(self.ctx, self.nocc, self.nvir)
+
+    def solve_window(self, omega0, delta, k, **kw):
+        return pp_solve_window(self.ctx, omega0, delta, k, self.nocc, self.nvir, **kw)
+
+    def solve_windows(self, omega0, delta, k, **kw):
+        return pp_solve_windows(self.ctx, omega0, delta, k, **kw)
+
+    def stats(self):
+        return pp_last_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            pp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

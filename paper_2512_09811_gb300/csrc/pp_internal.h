@@ -1,0 +1,143 @@
+// Internal declarations of the GB300 polarization-propagator library.
+// Layouts (all row-major, doubles unless stated):
+//   eps  [n]            orbital energies, occupied first
+//   gap  [o][v]         e_a - e_i
+//   Bov  [Q][o][v]      B[Q,i,a];   Boo [Q][o][o];   Bvv [Q][v][v]
+//   BvvP [v][Q][v]      BvvP[b][Q][d] = B[Q,b,d]     (one GEMM forms V B_Q for every Q)
+//   BooT [o][o][Q]      BooT[i][k][Q] = B[Q,i,k]     (contraction over (k, Q))
+//   GB   [2Q][o][v]     rows 0..Q-1: Bov + Gamma, rows Q..2Q-1: Bov
+//   Gam  [Q][o][v]      Gamma_Q[j,a] = sum_kc t_jk^ac B[Q,k,c]
+//   p_oo, q_oo [o][o]; p_vv, q_vv [v][v]: pair sums of the MP2 amplitudes
+//   supervectors [nvec][2][o][v] = half-vectors V[2 nvec][o][v]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+
+struct PPError {
+  pp_status st;
+  std::string msg;
+  PPError(pp_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+#define PP_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw PPError(e_ == cudaErrorMemoryAllocation ? PP_ENOMEM : PP_ECUDA,                  \
+                    std::string(#call) + " -> " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define PP_LAUNCH_CHECK(name)                                                                \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess) throw PPError(PP_ECUDA, std::string(name) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// grow-only device buffer
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t nbytes) {
+    if (nbytes <= bytes) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    PP_CUDA(cudaMalloc(&p, nbytes));
+    bytes = nbytes;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// generic strided FP64 GEMM with an inner reduction batch and an outer batch:
+//   C_b = alpha * sum_{t < nred} op(A_{b,t}) op(B_{b,t}) + beta * C_b
+// op(A) is M x K with element (m,k) at A + b*a_batch + t*a_red + m*a_m + k*a_k;
+// op(B) is K x N with element (k,n) at B + b*b_batch + t*b_red + k*b_k + n*b_n;
+// C element (m,n) at C + b*c_batch + m*c_m + n*c_n.
+// ---------------------------------------------------------------------------
+template <class T> struct GemmS {
+  int M = 0, N = 0, K = 0, nred = 1, nbatch = 1;
+  const T *A = nullptr;
+  long long a_m = 0, a_k = 0, a_red = 0, a_batch = 0;
+  const T *B = nullptr;
+  long long b_k = 0, b_n = 0, b_red = 0, b_batch = 0;
+  T *C = nullptr;
+  long long c_m = 0, c_n = 0, c_batch = 0;
+  T alpha = 1, beta = 0;
+};
+using GemmF64 = GemmS<double>;
+using GemmF32 = GemmS<float>;
+void gemm_f64(const GemmF64 &g, cudaStream_t s);
+void gemm_f32(const GemmF32 &g, cudaStream_t s);
+
+// T slab in FP64: rows (i - i0, c) for i in [i0, i0+ni), columns (j, d):
+// T[(ii*v + c)*ov + j*v + d] = t_ij^cd = ((ci|dj) - (cj|di)) / (e_i + e_j - e_c - e_d)
+void tslab_f64(const double *Bov, const double *eps, int o, int v, int Q, int i0, int ni, double *T,
+               cudaStream_t s);
+
+// elementwise helpers (sigma_f64.cu)
+void ew_copy_scale(double *y, const double *x, double a, long long n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// BF16 tensor-core (tcgen05) path, tc_gemm.cu
+// ---------------------------------------------------------------------------
+struct TcPlan;  // opaque
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct pp_ctx {
+  int o = 0, v = 0, Q = 0, n = 0;
+  long long ov = 0;
+  pp_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool has_mu = false;
+
+  // resident FP64 data
+  DevBuf eps, gap, Bov, Boo, Bvv, BvvP, BooT, GB, Gam, mu;
+  DevBuf p_oo, q_oo, p_vv, q_vv, diagA, diagS;
+
+  // FP64 sigma workspaces
+  DevBuf w_acc, w_cq, w_W, w_U, w_P, w_EF, w_tmp, w_T, w_Tw, w_V;
+  int sig_chunk = 2;  // half-vectors per chunk (even)
+  int slab_i = 1;     // occupied indices per T slab
+
+  // BF16 tensor-core path (lazily built)
+  TcPlan *tc = nullptr;
+
+  // solver workspaces
+  DevBuf s_V, s_MV, s_SV, s_X, s_MX, s_SX, s_D, s_MD, s_SD, s_G, s_gram, s_small, s_part, s_eig;
+
+  // stats of the last solve
+  int st_iters = 0;
+  long long st_sigvec = 0;
+  double st_sigma_ms = 0.0, st_solve_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// sigma_f64.cu
+void build_residency(pp_ctx *c, const double *Bd, const float *Bf);
+void precompute_f64(pp_ctx *c);
+void sigma_f64(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d);
+// tc_gemm.cu
+void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split);
+void tc_destroy(pp_ctx *c);
+// solver.cu
+pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta, const int *k,
+                             double *omega, double *osc, double *resid, double *vecs, int *nfound);
+// dispatch of one sigma application (solver and C ABI)
+void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec);

@@ -1,0 +1,1147 @@
+// Interior-root window solver of Sec. 2.5.
+//
+// For each window the solver keeps an orthonormal basis V (FP64) together
+// with M V and Sigma V.  Each outer iteration
+//   1. Rayleigh-Ritz on the projected pencil (V^T M V, V^T Sigma V): M is
+//      positive definite for a stable RPA problem, so V^T M V = L L^T and the
+//      symmetric matrix L^-1 V^T Sigma V L^-T is diagonalised (parallel cyclic
+//      Jacobi); the Ritz values theta = 1/mu nearest the window shift become
+//      the targets;
+//   2. for each target, in order, the folded-spectrum vector of Sec. 2.5:
+//        y = argmin <y|(M - w Sigma)^2|y> / <y|y>  over y in span(V),
+//      with the fold centre w set to the Rayleigh quotient of y (four updates,
+//      three inverse-iteration solves each), and y
+//      kept Sigma-orthogonal to the earlier targets (a penalty on the
+//      constraint directions).  With w equal to a root the minimum is the null
+//      vector of Sec. 2.5; with S != 1 a fixed w would not converge to an
+//      eigenvector, so the centre follows the Ritz value;
+//   3. residuals r = M y - theta Sigma y; for unconverged targets the
+//      inverse-Krylov direction is one weighted-Jacobi sweep (Sec. 2.5.2, the
+//      splitting M - theta Sigma = D + F) on the correction equation
+//      (M - theta Sigma) t = -r from t = 0, i.e. t = -D^-1 r;
+//   4. one sigma batch for all windows' directions, CGS2 against V (M V and
+//      Sigma V updated by the same combinations), thick restart when full.
+#include "pp_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+
+namespace {
+
+constexpr int MAXM = 112;  // largest subspace the shared-memory eigensolver takes
+
+// ---- tall-skinny Gram: partial[blk][i][j] = sum_{l in chunk} A_i[l] B_j[l] -------------
+constexpr int GR_ROWS = 16;
+__global__ void __launch_bounds__(256) k_gram(const double *__restrict__ A, long long lda, int p,
+                                              const double *__restrict__ B, long long ldb, int q,
+                                              long long L, long long chunk, double *__restrict__ part) {
+  __shared__ double As[MAXM][GR_ROWS + 1];
+  __shared__ double Bs[MAXM][GR_ROWS + 1];
+  const long long l0 = blockIdx.x * chunk;
+  const long long l1 = min(L, l0 + chunk);
+  const int npair = p * q;
+  double acc[(MAXM * MAXM + 255) / 256];
+  const int mine = (npair - (int)threadIdx.x + 255) / 256;
+  for (int e = 0; e < (MAXM * MAXM + 255) / 256; ++e) acc[e] = 0.0;
+  for (long long r0 = l0; r0 < l1; r0 += GR_ROWS) {
+    for (int idx = threadIdx.x; idx < p * GR_ROWS; idx += 256) {
+      int i = idx / GR_ROWS, rr = idx % GR_ROWS;
+      long long l = r0 + rr;
+      As[i][rr] = (l < l1) ? A[i * lda + l] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < q * GR_ROWS; idx += 256) {
+      int j = idx / GR_ROWS, rr = idx % GR_ROWS;
+      long long l = r0 + rr;
+      Bs[j][rr] = (l < l1) ? B[j * ldb + l] : 0.0;
+    }
+    __syncthreads();
+    for (int e = 0; e < mine; ++e) {
+      int pr = threadIdx.x + e * 256;
+      int i = pr / q, j = pr % q;
+      double s = acc[e];
+#pragma unroll
+      for (int rr = 0; rr < GR_ROWS; ++rr) s = fma(As[i][rr], Bs[j][rr], s);
+      acc[e] = s;
+    }
+    __syncthreads();
+  }
+  for (int e = 0; e < mine; ++e) {
+    int pr = threadIdx.x + e * 256;
+    part[(long long)blockIdx.x * npair + pr] = acc[e];
+  }
+}
+__global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int p, int q,
+                              double *__restrict__ G, int ldg, double alpha, double beta) {
+  int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= p * q) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)b * p * q + pr];
+  int i = pr / q, j = pr % q;
+  double *g = G + (long long)i * ldg + j;
+  *g = alpha * s + (beta != 0.0 ? beta * (*g) : 0.0);
+}
+
+// ---- parallel cyclic Jacobi for a symmetric m x m matrix (m <= MAXM) -----------------
+// out: evals ascending in lam[m]; eigenvectors as rows E[j*m + i] (component i of vector j)
+__global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ Gin, int m,
+                                                    double *__restrict__ lam,
+                                                    double *__restrict__ E, int max_sweeps) {
+  extern __shared__ double sm[];
+  const int mp = (m + 1) & ~1;
+  double *A = sm;            // mp x mp
+  double *V = sm + mp * mp;  // mp x mp, eigenvectors as columns
+  __shared__ double cs[MAXM / 2], sn[MAXM / 2];
+  __shared__ int pp[MAXM / 2], qq[MAXM / 2];
+  __shared__ double red[512];
+  __shared__ int perm[MAXM];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double diag_big = 0.0;
+  for (int idx = tid; idx < mp * mp; idx += nt) {
+    int i = idx / mp, j = idx % mp;
+    double a;
+    if (i < m && j < m) a = 0.5 * (Gin[i * m + j] + Gin[j * m + i]);
+    else a = 0.0;
+    A[idx] = a;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // a padding row gets a diagonal larger than every eigenvalue so it sorts last
+  if (mp != m) {
+    double s = 0.0;
+    for (int idx = tid; idx < m * m; idx += nt) s += fabs(A[(idx / m) * mp + idx % m]);
+    red[tid] = s;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    diag_big = 1.0 + 2.0 * red[0];
+    if (tid == 0) A[(mp - 1) * mp + (mp - 1)] = diag_big;
+    __syncthreads();
+  }
+  const int half = mp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // off-diagonal and total norms
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < mp * mp; idx += nt) {
+      double a = A[idx];
+      tot += a * a;
+      if (idx / mp != idx % mp) off += a * a;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    off = red[0];
+    __syncthreads();
+    red[tid] = tot;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    tot = red[0];
+    __syncthreads();
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int r = 0; r < mp - 1; ++r) {
+      if (tid < half) {
+        int k = tid;
+        int a, b;
+        if (k == 0) {
+          a = 0;
+          b = (r % (mp - 1)) + 1;
+        } else {
+          a = ((r + k) % (mp - 1)) + 1;
+          b = ((r - k + (mp - 1)) % (mp - 1)) + 1;
+        }
+        int p = min(a, b), q = max(a, b);
+        double apq = A[p * mp + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300) {
+          double app = A[p * mp + p], aqq = A[q * mp + q];
+          double theta = (aqq - app) / (2.0 * apq);
+          double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+        }
+        cs[k] = c;
+        sn[k] = s;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = tid; idx < half * mp; idx += nt) {
+        int k = idx / mp, j = idx % mp;
+        int p = pp[k], q = qq[k];
+        double c = cs[k], s = sn[k];
+        double ap = A[p * mp + j], aq = A[q * mp + j];
+        A[p * mp + j] = c * ap - s * aq;
+        A[q * mp + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = tid; idx < half * mp; idx += nt) {
+        int k = idx / mp, i = idx % mp;
+        int p = pp[k], q = qq[k];
+        double c = cs[k], s = sn[k];
+        double ap = A[i * mp + p], aq = A[i * mp + q];
+        A[i * mp + p] = c * ap - s * aq;
+        A[i * mp + q] = s * ap + c * aq;
+        double vp = V[i * mp + p], vq = V[i * mp + q];
+        V[i * mp + p] = c * vp - s * vq;
+        V[i * mp + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    for (int i = 0; i < m; ++i) {  // selection sort of the m real eigenvalues
+      int best = i;
+      for (int j = i + 1; j < m; ++j)
+        if (A[perm[j] * mp + perm[j]] < A[perm[best] * mp + perm[best]]) best = j;
+      int t = perm[i];
+      perm[i] = perm[best];
+      perm[best] = t;
+    }
+  }
+  __syncthreads();
+  // drop the padding column: if it was not the last after sorting the pad index is m
+  for (int j = tid; j < m; j += nt) lam[j] = A[perm[j] * mp + perm[j]];
+  for (int idx = tid; idx < m * m; idx += nt) {
+    int j = idx / m, i = idx % m;
+    E[idx] = V[i * mp + perm[j]];
+  }
+}
+
+// ---- per-column reductions ------------------------------------------------------------
+__device__ double block_sum(double x, double *red) {
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// per column j: out[j*3 + 0..2] = (x.Mx, x.Sx, x.x)
+__global__ void k_ritz_dots(const double *__restrict__ X, const double *__restrict__ MX,
+                            const double *__restrict__ SX, long long L, double *__restrict__ out) {
+  __shared__ double red[256];
+  const long long off = (long long)blockIdx.x * L;
+  double a = 0, b = 0, c = 0;
+  for (long long l = threadIdx.x; l < L; l += blockDim.x) {
+    double x = X[off + l];
+    a += x * MX[off + l];
+    b += x * SX[off + l];
+    c += x * x;
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  c = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    out[blockIdx.x * 3 + 0] = a;
+    out[blockIdx.x * 3 + 1] = b;
+    out[blockIdx.x * 3 + 2] = c;
+  }
+}
+
+// per column j: |MX - theta_j SX|^2 into rnorm[j]; correction direction of one Jacobi sweep on
+// (M - theta_j Sigma) t = -r:  t = -r / D with D = [dA; dA] - theta_j [dS; -dS], |D| floored
+// at floor_ keeping its sign.
+__global__ void k_resid_dir(const double *__restrict__ X, const double *__restrict__ MX,
+                            const double *__restrict__ SX, const double *__restrict__ theta,
+                            const double *__restrict__ dA, const double *__restrict__ dS,
+                            long long ov, double floor_, double *__restrict__ Dout,
+                            double *__restrict__ rnorm) {
+  __shared__ double red[256];
+  const long long L = 2 * ov;
+  const long long off = (long long)blockIdx.x * L;
+  const double th = theta[blockIdx.x];
+  double acc = 0.0;
+  for (long long l = threadIdx.x; l < L; l += blockDim.x) {
+    double r = MX[off + l] - th * SX[off + l];
+    acc += r * r;
+    if (Dout) {
+      long long e = l % ov;
+      double sg = (l < ov) ? 1.0 : -1.0;
+      double D = dA[e] - th * sg * dS[e];
+      if (fabs(D) < floor_) D = (D >= 0 ? floor_ : -floor_);
+      Dout[off + l] = -r / D;
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) rnorm[blockIdx.x] = acc;
+}
+
+// y_j <- y_j * s for three arrays, with s = 1/sqrt(nrm[0])
+__global__ void k_scale3(double *__restrict__ a, double *__restrict__ b, double *__restrict__ c,
+                         long long L, const double *__restrict__ nrm2) {
+  double s = 1.0 / sqrt(nrm2[0]);
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < L;
+       l += (long long)gridDim.x * blockDim.x) {
+    a[l] *= s;
+    b[l] *= s;
+    c[l] *= s;
+  }
+}
+
+// oscillator strengths: z = x / sqrt(x^T Sigma x); out[j] = (2/3) theta sum_c (mu_c . (X + Y))^2
+__global__ void k_osc(const double *__restrict__ X, const double *__restrict__ mu, long long ov,
+                      const double *__restrict__ theta, const double *__restrict__ xsx,
+                      double *__restrict__ out) {
+  __shared__ double red[256];
+  const long long off = (long long)blockIdx.x * 2 * ov;
+  double m0 = 0, m1 = 0, m2 = 0;
+  for (long long e = threadIdx.x; e < ov; e += blockDim.x) {
+    double s = X[off + e] + X[off + ov + e];
+    m0 += mu[e] * s;
+    m1 += mu[ov + e] * s;
+    m2 += mu[2 * ov + e] * s;
+  }
+  m0 = block_sum(m0, red);
+  m1 = block_sum(m1, red);
+  m2 = block_sum(m2, red);
+  if (threadIdx.x == 0) {
+    double nrm = xsx[blockIdx.x];
+    out[blockIdx.x] = (2.0 / 3.0) * theta[blockIdx.x] * (m0 * m0 + m1 * m1 + m2 * m2) / fabs(nrm);
+  }
+}
+
+__global__ void k_unit_vectors(double *__restrict__ V, long long L, const int *__restrict__ idx, int nb) {
+  int j = blockIdx.y;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < L;
+       l += (long long)gridDim.x * blockDim.x)
+    V[j * L + l] = (l == idx[j]) ? 1.0 : 0.0;
+}
+
+
+// ---- small dense linear algebra on the projected pencil (one CTA) -------------------
+// Cholesky of a symmetric positive definite m x m matrix held in shared memory
+// (row stride ld), computed by warp 0.  Lower factor in place; diag in dL.
+// Returns false (uniformly on warp 0) if a pivot is not positive.
+__device__ bool warp_cholesky(double *G, int ld, int m, double *dL) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < m; ++k) {
+    double akk = G[k * ld + k];
+    if (!(akk > 0.0)) return false;
+    double lkk = sqrt(akk);
+    if (lane == 0) dL[k] = lkk;
+    for (int i = k + 1 + lane; i < m; i += 32) G[i * ld + k] /= lkk;
+    __syncwarp();
+    for (int i = k + 1 + lane; i < m; i += 32) {
+      double lik = G[i * ld + k];
+      for (int j = k + 1; j <= i; ++j) G[i * ld + j] -= lik * G[j * ld + k];
+    }
+    __syncwarp();
+  }
+  return true;
+}
+// solve L L^T x = c in place (warp 0), L from warp_cholesky
+__device__ void warp_chol_solve(const double *G, int ld, int m, const double *dL, double *c) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < m; ++k) {
+    double yk = c[k] / dL[k];
+    __syncwarp();
+    if (lane == 0) c[k] = yk;
+    for (int i = k + 1 + lane; i < m; i += 32) c[i] -= G[i * ld + k] * yk;
+    __syncwarp();
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    double xk = c[k] / dL[k];
+    __syncwarp();
+    if (lane == 0) c[k] = xk;
+    for (int i = lane; i < k; i += 32) c[i] -= G[k * ld + i] * xk;
+    __syncwarp();
+  }
+}
+
+// Rayleigh-Ritz setup: Hm = L L^T, Cw = L^-1 Hs L^-T.  L written to Lout (m x m, row-major).
+__global__ void __launch_bounds__(256) k_chol_rr(const double *__restrict__ Hm,
+                                                 const double *__restrict__ Hs, int m,
+                                                 double *__restrict__ Lout, double *__restrict__ Y,
+                                                 double *__restrict__ Cw, int *__restrict__ status) {
+  extern __shared__ double sm[];
+  const int ld = m + 1;
+  double *G = sm;
+  double *dL = G + m * ld;
+  __shared__ int ok_s;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, k = idx % m;
+    G[i * ld + k] = 0.5 * (Hm[i * m + k] + Hm[k * m + i]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    bool ok = warp_cholesky(G, ld, m, dL);
+    if (threadIdx.x == 0) ok_s = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (!ok_s) {
+    if (threadIdx.x == 0) *status = 1;
+    return;
+  }
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, k = idx % m;
+    Lout[idx] = (k < i) ? G[i * ld + k] : (k == i ? dL[i] : 0.0);
+  }
+  // Y = L^-1 Hs, column by column (one thread per column)
+  for (int col = threadIdx.x; col < m; col += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double acc = 0.5 * (Hs[i * m + col] + Hs[col * m + i]);
+      for (int k = 0; k < i; ++k) acc -= G[i * ld + k] * Y[k * m + col];
+      Y[i * m + col] = acc / dL[i];
+    }
+  }
+  __syncthreads();
+  // Cw^T = L^-1 Y^T: row r of Cw solves L z = (row r of Y)
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double acc = Y[r * m + i];
+      for (int k = 0; k < i; ++k) acc -= G[i * ld + k] * Cw[r * m + k];
+      Cw[r * m + i] = acc / dL[i];
+    }
+  }
+}
+
+// E = L^-T W (generalised eigenvectors, E^T Hm E = 1), theta = 1/mu, the ncol columns with
+// theta nearest the shift (ascending distance), each scaled to unit Euclidean norm.
+__global__ void __launch_bounds__(128) k_rr_select(const double *__restrict__ Lm,
+                                                   const double *__restrict__ mu,
+                                                   const double *__restrict__ W, int m,
+                                                   double shift, int ncol,
+                                                   double *__restrict__ Ework,
+                                                   double *__restrict__ theta_out,
+                                                   double *__restrict__ Eout) {
+  __shared__ int order[MAXM];
+  __shared__ double dist[MAXM];
+  // back substitution per eigenvector j: L^T e = w
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double *w = W + (long long)j * m;
+    double *e = Ework + (long long)j * m;
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = w[i];
+      for (int k = i + 1; k < m; ++k) acc -= Lm[k * m + i] * e[k];
+      e[i] = acc / Lm[i * m + i];
+    }
+    double th = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
+    dist[j] = fabs(th - shift);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < m; ++j) order[j] = j;
+    for (int i = 0; i < ncol && i < m; ++i) {
+      int best = i;
+      for (int j = i + 1; j < m; ++j)
+        if (dist[order[j]] < dist[order[best]]) best = j;
+      int t = order[i];
+      order[i] = order[best];
+      order[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+    int j = order[t];
+    const double *e = Ework + (long long)j * m;
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += e[i] * e[i];
+    nrm = 1.0 / sqrt(nrm);
+    for (int i = 0; i < m; ++i) Eout[(long long)t * m + i] = e[i] * nrm;
+    theta_out[t] = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
+  }
+}
+
+__device__ double blk_sum(double x, double *red) {
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Folded-spectrum vectors with deflation (one CTA, 256 threads).  For target j:
+//   w <- th0[j]; repeat reps times:
+//     G(w) = (MV - w SV)^T (MV - w SV) = Gmm - w (Gms + Gms^T) + w^2 Gss,
+//     restricted to coefficients Euclidean-orthogonal to Hs c_i (i < j) by a penalty,
+//     c <- smallest eigenvector (inverse iteration from the previous c), w <- c^T Hm c / c^T Hs c.
+__global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
+                                                 const double *__restrict__ Hs,
+                                                 const double *__restrict__ Gmm,
+                                                 const double *__restrict__ Gms,
+                                                 const double *__restrict__ Gss, int m, int b,
+                                                 int reps, const double *__restrict__ th0,
+                                                 const double *__restrict__ C0,
+                                                 double *__restrict__ Cout,
+                                                 double *__restrict__ thout,
+                                                 int *__restrict__ status) {
+  extern __shared__ double sm[];
+  const int ld = m + 1;
+  double *G = sm;               // m x ld
+  double *Qc = G + m * ld;      // b x m, orthonormal constraint directions
+  double *GQ = Qc + b * m;      // m x b
+  double *c = GQ + m * b;       // m
+  double *t1 = c + m;           // m
+  double *dL = t1 + m;          // m
+  __shared__ double red[256];
+  __shared__ double qgq[32 * 32];
+  __shared__ int ok_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < b; ++j) {
+    double w = th0[j];
+    for (int i = tid; i < m; i += nt) c[i] = C0[(long long)j * m + i];
+    __syncthreads();
+    for (int rep = 0; rep < reps; ++rep) {
+      double tr = 0.0;
+      for (int idx = tid; idx < m * m; idx += nt) {
+        int i = idx / m, k = idx % m;
+        double g = 0.5 * (Gmm[i * m + k] + Gmm[k * m + i]) - w * (Gms[i * m + k] + Gms[k * m + i]) +
+                   w * w * 0.5 * (Gss[i * m + k] + Gss[k * m + i]);
+        G[i * ld + k] = g;
+        if (i == k) tr += g;
+      }
+      tr = blk_sum(tr, red);
+      const double gamma = 10.0 * tr + 1e-300, delta = 1e-14 * tr + 1e-300;
+      if (j > 0) {
+        // GQ = G Q^T (m x j); qgq = Q G Q^T (j x j)
+        for (int idx = tid; idx < m * j; idx += nt) {
+          int i = idx / j, p = idx % j;
+          double s = 0.0;
+          for (int k = 0; k < m; ++k) s += G[i * ld + k] * Qc[p * m + k];
+          GQ[i * b + p] = s;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < j * j; idx += nt) {
+          int p = idx / j, q = idx % j;
+          double s = 0.0;
+          for (int i = 0; i < m; ++i) s += Qc[p * m + i] * GQ[i * b + q];
+          qgq[p * 32 + q] = s;
+        }
+        __syncthreads();
+        // G <- (1 - QQ^T) G (1 - QQ^T) + gamma QQ^T
+        for (int idx = tid; idx < m * m; idx += nt) {
+          int i = idx / m, k = idx % m;
+          double g = G[i * ld + k];
+          for (int p = 0; p < j; ++p) {
+            double qi = Qc[p * m + i], qk = Qc[p * m + k];
+            g -= GQ[i * b + p] * qk + qi * GQ[k * b + p];
+            g += gamma * qi * qk;
+            for (int q = 0; q < j; ++q) g += qi * qgq[p * 32 + q] * Qc[q * m + k];
+          }
+          G[i * ld + k] = g;
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < m; i += nt) G[i * ld + i] += delta;
+      __syncthreads();
+      if (tid < 32) {
+        bool ok = warp_cholesky(G, ld, m, dL);
+        if (tid == 0) ok_s = ok ? 1 : 0;
+      }
+      __syncthreads();
+      if (!ok_s) {
+        if (tid == 0) *status = 2;
+        break;
+      }
+      for (int itv = 0; itv < 4; ++itv) {
+        // project c off the constraint directions and normalise
+        for (int p = 0; p < j; ++p) {
+          double s = 0.0;
+          for (int i = tid; i < m; i += nt) s += Qc[p * m + i] * c[i];
+          s = blk_sum(s, red);
+          for (int i = tid; i < m; i += nt) c[i] -= s * Qc[p * m + i];
+          __syncthreads();
+        }
+        double nn = 0.0;
+        for (int i = tid; i < m; i += nt) nn += c[i] * c[i];
+        nn = blk_sum(nn, red);
+        if (!(nn > 0.0)) nn = 1.0;
+        for (int i = tid; i < m; i += nt) c[i] /= sqrt(nn);
+        __syncthreads();
+        if (itv == 3) break;
+        if (tid < 32) warp_chol_solve(G, ld, m, dL, c);
+        __syncthreads();
+      }
+      // fold centre follows the Rayleigh quotient of the folded vector
+      double nm = 0.0, ns = 0.0;
+      for (int i = tid; i < m; i += nt) {
+        double hm = 0.0, hs = 0.0;
+        for (int k = 0; k < m; ++k) {
+          hm += Hm[i * m + k] * c[k];
+          hs += Hs[i * m + k] * c[k];
+        }
+        nm += c[i] * hm;
+        ns += c[i] * hs;
+      }
+      nm = blk_sum(nm, red);
+      ns = blk_sum(ns, red);
+      if (fabs(ns) > 1e-300) w = nm / ns;
+    }
+    for (int i = tid; i < m; i += nt) Cout[(long long)j * m + i] = c[i];
+    if (tid == 0) thout[j] = w;
+    // new constraint direction: Hs c, orthonormalised against the previous ones (twice)
+    for (int i = tid; i < m; i += nt) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += Hs[i * m + k] * c[k];
+      t1[i] = s;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p = 0; p < j; ++p) {
+        double s = 0.0;
+        for (int i = tid; i < m; i += nt) s += Qc[p * m + i] * t1[i];
+        s = blk_sum(s, red);
+        for (int i = tid; i < m; i += nt) t1[i] -= s * Qc[p * m + i];
+        __syncthreads();
+      }
+    double nn = 0.0;
+    for (int i = tid; i < m; i += nt) nn += t1[i] * t1[i];
+    nn = blk_sum(nn, red);
+    double inv = (nn > 1e-300) ? 1.0 / sqrt(nn) : 0.0;
+    for (int i = tid; i < m; i += nt) Qc[j * m + i] = t1[i] * inv;
+    __syncthreads();
+  }
+}
+
+// modified Gram-Schmidt of ncol coefficient vectors K[t][m] (Euclidean); the first nout
+// independent ones go to Q[t][m]; *nkept receives their count.
+__global__ void __launch_bounds__(128) k_mgs(const double *__restrict__ K, int m, int ncol, int nout,
+                                             double *__restrict__ Qo, int *__restrict__ nkept) {
+  __shared__ double red[128];
+  __shared__ double v[MAXM];
+  int kept = 0;
+  for (int t = 0; t < ncol && kept < nout; ++t) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = K[(long long)t * m + i];
+    __syncthreads();
+    double n0 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) n0 += v[i] * v[i];
+    n0 = blk_sum(n0, red);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p = 0; p < kept; ++p) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) s += Qo[(long long)p * m + i] * v[i];
+        s = blk_sum(s, red);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] -= s * Qo[(long long)p * m + i];
+        __syncthreads();
+      }
+    double n1 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) n1 += v[i] * v[i];
+    n1 = blk_sum(n1, red);
+    if (n1 > 1e-20 * n0 && n1 > 0.0) {
+      double inv = 1.0 / sqrt(n1);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) Qo[(long long)kept * m + i] = v[i] * inv;
+      ++kept;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nkept = kept;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Solver {
+  pp_ctx *c;
+  cudaStream_t s;
+  long long L;  // 2 ov
+  double *part = nullptr;
+  size_t part_elems = 0;
+
+  void gram(const double *A, long long lda, int p, const double *B, long long ldb, int q,
+            double *G, int ldg, double alpha = 1.0, double beta = 0.0) {
+    long long nblk = std::min<long long>(std::max<long long>(1, L / 1024), 296);
+    long long chunk = (L + nblk - 1) / nblk;
+    chunk = ((chunk + GR_ROWS - 1) / GR_ROWS) * GR_ROWS;
+    nblk = (L + chunk - 1) / chunk;
+    size_t need = (size_t)nblk * p * q;
+    if (need > part_elems) throw PPError(PP_ECUDA, "gram scratch too small");
+    k_gram<<<(unsigned)nblk, 256, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, part);
+    PP_LAUNCH_CHECK("k_gram");
+    k_gram_reduce<<<(p * q + 255) / 256, 256, 0, s>>>(part, (int)nblk, p, q, G, ldg, alpha, beta);
+    PP_LAUNCH_CHECK("k_gram_reduce");
+  }
+  // Y[:, 0..q) (+)= V[:, 0..m) C with C[j*ldc + i] (column j of C), columns of length L
+  void combine(const double *V, int m, const double *C, int ldc, int q, double *Y, double alpha,
+               double beta) {
+    GemmF64 g;
+    g.M = (int)L; g.N = q; g.K = m;
+    g.A = V; g.a_m = 1; g.a_k = L;
+    g.B = C; g.b_k = 1; g.b_n = ldc;
+    g.C = Y; g.c_m = 1; g.c_n = L;
+    g.alpha = alpha; g.beta = beta;
+    gemm_f64(g, s);
+  }
+};
+
+struct Window {
+  double omega0 = 0, delta = 0;
+  int k = 0;
+  double shift = 0;
+  int nev = 0, b = 0;
+  int m = 0;
+  double *V = nullptr, *MV = nullptr, *SV = nullptr;  // [m_max][L]
+  double *X = nullptr, *MX = nullptr, *SX = nullptr;  // [64][L]
+  double *Hm, *Hs, *Gmm, *Gms, *Gss, *Lm, *Yw, *Cw, *mu, *W, *Ew, *Esel, *thsel, *Cref, *thref, *Kc, *Qk;
+  int *dstat, *dkept;
+  std::vector<double> h_theta, h_res, h_xsx;
+  std::vector<int> order;   // Ritz columns sorted by distance of theta to the shift
+  std::vector<int> active;  // columns that get a direction this iteration
+  bool done = false;
+  int adjust = 0;
+};
+
+}  // namespace
+
+void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec) {
+  if (nvec <= 0) return;
+  if (prec == PP_FP64) sigma_f64(c, nvec, Zd, sig_d, met_d);
+  else sigma_bf16(c, nvec, Zd, sig_d, met_d, prec == PP_BF16X3);
+}
+
+pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta,
+                             const int *kk, double *omega_out, double *osc_out, double *resid_out,
+                             double *vecs_out, int *nfound) {
+  cudaStream_t s = c->stream;
+  const long long ov = c->ov, L = 2 * ov;
+  const int prec = c->opt.prec;
+  Solver sv{c, s, L};
+  const int m_max = std::min<int>(std::min(c->opt.m_max, MAXM), (int)L);
+  const int bcap = std::max(1, std::min(32, m_max / 3));
+  std::vector<double> hA(ov), hS(ov);
+  PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(hS.data(), c->diagS.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> ratio(ov);
+  for (long long p = 0; p < ov; ++p) ratio[p] = hA[p] / hS[p];
+
+  std::vector<Window> W(nwin);
+  for (int w = 0; w < nwin; ++w) {
+    Window &wi = W[w];
+    wi.omega0 = omega0[w];
+    wi.delta = delta ? delta[w] : 0.0;
+    wi.k = kk[w];
+    if (wi.k <= 0) throw PPError(PP_EINVAL, "k must be positive");
+    if (c->opt.select == 1) {
+      wi.shift = wi.omega0;
+      wi.nev = wi.k + 2;
+    } else {
+      // centre the targets on the expected k lowest roots above omega0 (diagonal estimate)
+      std::vector<double> above;
+      for (long long p = 0; p < ov; ++p)
+        if (ratio[p] >= wi.omega0) above.push_back(ratio[p]);
+      std::sort(above.begin(), above.end());
+      double rk = above.empty() ? wi.omega0 : above[std::min<size_t>(above.size() - 1, wi.k - 1)];
+      wi.shift = wi.omega0 + 0.5 * (rk - wi.omega0);
+      wi.nev = wi.k + std::max(2, wi.k / 2);
+    }
+    wi.nev = std::min<int>(wi.nev, (int)L);
+    wi.b = std::min(bcap, std::max(wi.nev + 2, c->opt.block));
+    wi.b = std::min<int>(wi.b, (int)L);
+    wi.nev = std::min(wi.nev, wi.b);
+  }
+  // device memory: per window basis (3 m_max vectors), Ritz block (3 x 64), small matrices
+  const size_t vecbytes = sizeof(double) * (size_t)L;
+  const size_t mm = (size_t)MAXM * MAXM;
+  const size_t per_win = vecbytes * (3 * (size_t)m_max + 3 * 64) + sizeof(double) * 20 * mm + 64;
+  c->s_V.ensure(per_win * nwin);
+  c->s_D.ensure(vecbytes * 32 * nwin);
+  c->s_MD.ensure(vecbytes * 32 * nwin);
+  c->s_SD.ensure(vecbytes * 32 * nwin);
+  sv.part_elems = (size_t)296 * mm;
+  c->s_part.ensure(sizeof(double) * sv.part_elems);
+  sv.part = c->s_part.as<double>();
+  c->s_small.ensure(sizeof(double) * 8192);
+  double *scratch = c->s_small.as<double>();
+  int *iscratch = reinterpret_cast<int *>(scratch + 4096);
+  {
+    char *base = c->s_V.as<char>();
+    for (int w = 0; w < nwin; ++w) {
+      char *p = base + per_win * w;
+      Window &wi = W[w];
+      auto take = [&](size_t bytes) {
+        char *q = p;
+        p += bytes;
+        return (double *)q;
+      };
+      wi.V = take(vecbytes * m_max);
+      wi.MV = take(vecbytes * m_max);
+      wi.SV = take(vecbytes * m_max);
+      wi.X = take(vecbytes * 64);
+      wi.MX = take(vecbytes * 64);
+      wi.SX = take(vecbytes * 64);
+      double **mats[] = {&wi.Hm, &wi.Hs, &wi.Gmm, &wi.Gms, &wi.Gss, &wi.Lm, &wi.Yw, &wi.Cw, &wi.mu,
+                         &wi.W, &wi.Ew, &wi.Esel, &wi.thsel, &wi.Cref, &wi.thref, &wi.Kc, &wi.Qk};
+      for (double **q : mats) *q = take(sizeof(double) * mm);
+      wi.dstat = (int *)take(sizeof(double) * mm);
+      wi.dkept = wi.dstat + 4;
+    }
+  }
+  const int ld = MAXM + 1;
+  const int smem_jac = 2 * MAXM * MAXM * (int)sizeof(double);
+  const int smem_chol = (MAXM * ld + MAXM) * (int)sizeof(double);
+  const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
+  PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
+  PP_CUDA(cudaFuncSetAttribute(k_chol_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
+  PP_CUDA(cudaFuncSetAttribute(k_refined, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ref));
+
+  cudaEvent_t e0 = c->ev0, e1 = c->ev1;
+  c->st_iters = 0;
+  c->st_sigvec = 0;
+  c->st_sigma_ms = 0.0;
+  float ms = 0.f;
+  // mixed precision: BF16 sigma to a loose tolerance, then the split form (FP32-level)
+  const bool refine = (prec == PP_BF16) && c->opt.refine;
+  int cur_prec = prec;
+  auto run_sigma = [&](int nv, const double *Z, double *Sg, double *Mt) {
+    PP_CUDA(cudaEventRecord(e0, s));
+    apply_sigma(c, nv, Z, Sg, Mt, cur_prec);
+    PP_CUDA(cudaEventRecord(e1, s));
+    PP_CUDA(cudaEventSynchronize(e1));
+    PP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    c->st_sigma_ms += ms;
+    c->st_sigvec += nv;
+  };
+
+  // ---- initial blocks: unit vectors on the diagonal entries nearest each shift
+  {
+    int off = 0;
+    std::vector<int> hidx;
+    for (int w = 0; w < nwin; ++w) {
+      Window &wi = W[w];
+      std::vector<long long> order(ov);
+      std::iota(order.begin(), order.end(), 0);
+      const long long nb = std::min<long long>(wi.b, ov);
+      std::partial_sort(order.begin(), order.begin() + nb, order.end(), [&](long long a, long long b2) {
+        double da = fabs(ratio[a] - wi.shift), db = fabs(ratio[b2] - wi.shift);
+        return da < db || (da == db && a < b2);
+      });
+      for (int j = 0; j < wi.b; ++j) hidx.push_back((int)(j < nb ? order[j] : ov + order[j - nb]));
+      off += wi.b;
+    }
+    PP_CUDA(cudaMemcpyAsync(iscratch, hidx.data(), sizeof(int) * hidx.size(), cudaMemcpyHostToDevice, s));
+    double *D = c->s_D.as<double>();
+    k_unit_vectors<<<dim3(64, off), 256, 0, s>>>(D, L, iscratch, off);
+    PP_LAUNCH_CHECK("k_unit_vectors");
+    run_sigma(off, D, c->s_MD.as<double>(), c->s_SD.as<double>());
+    off = 0;
+    for (int w = 0; w < nwin; ++w) {
+      Window &wi = W[w];
+      PP_CUDA(cudaMemcpyAsync(wi.V, D + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.MV, c->s_MD.as<double>() + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.SV, c->s_SD.as<double>() + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
+      wi.m = wi.b;
+      off += wi.b;
+    }
+  }
+
+  const int max_iter = std::max(1, c->opt.max_iter);
+  const double tol_final = c->opt.res_tol;
+  double tol = refine ? std::max(tol_final, 1e-4) : tol_final;
+  const char *log_env = std::getenv("PP_LOG");
+  const bool log_on = log_env && log_env[0] && log_env[0] != '0';
+  pp_status fail = PP_OK;
+  bool all_done = false;
+  for (int it = 0; it < max_iter && !all_done && fail == PP_OK; ++it) {
+    all_done = true;
+    int off = 0;
+    for (int w = 0; w < nwin; ++w) {
+      Window &wi = W[w];
+      if (wi.done) continue;
+      const int m = wi.m;
+      const int b = std::min(wi.b, m);
+      // projected pencil and folded Gram matrices
+      sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
+      sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
+      sv.gram(wi.MV, L, m, wi.MV, L, m, wi.Gmm, m);
+      sv.gram(wi.MV, L, m, wi.SV, L, m, wi.Gms, m);
+      sv.gram(wi.SV, L, m, wi.SV, L, m, wi.Gss, m);
+      PP_CUDA(cudaMemsetAsync(wi.dstat, 0, sizeof(int) * 4, s));
+      k_chol_rr<<<1, 256, (m * (m + 1) + m) * sizeof(double), s>>>(wi.Hm, wi.Hs, m, wi.Lm, wi.Yw, wi.Cw, wi.dstat);
+      PP_LAUNCH_CHECK("k_chol_rr");
+      int mp = (m + 1) & ~1;
+      k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 40);
+      PP_LAUNCH_CHECK("k_jacobi_eig");
+      const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+      k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);
+      PP_LAUNCH_CHECK("k_rr_select");
+      k_refined<<<1, 256, (m * (m + 1) + 2 * b * m + 3 * m) * sizeof(double), s>>>(
+          wi.Hm, wi.Hs, wi.Gmm, wi.Gms, wi.Gss, m, b, 4, wi.thsel, wi.Esel, wi.Cref, wi.thref, wi.dstat);
+      PP_LAUNCH_CHECK("k_refined");
+      sv.combine(wi.V, m, wi.Cref, m, b, wi.X, 1.0, 0.0);
+      sv.combine(wi.MV, m, wi.Cref, m, b, wi.MX, 1.0, 0.0);
+      sv.combine(wi.SV, m, wi.Cref, m, b, wi.SX, 1.0, 0.0);
+      double *dots = scratch;  // [b][3]
+      double *theta_d = scratch + 3 * 64;
+      double *rn = scratch + 4 * 64;
+      k_ritz_dots<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, L, dots);
+      PP_LAUNCH_CHECK("k_ritz_dots");
+      std::vector<double> hd(3 * b);
+      int hstat[4];
+      PP_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 3 * b, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaMemcpyAsync(hstat, wi.dstat, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      if (hstat[0] == 1) {
+        fail = PP_EUNSTABLE;  // V^T M V not positive definite: M is not positive definite
+        c->err = "projected M is not positive definite (unstable RPA problem)";
+        break;
+      }
+      wi.h_theta.assign(b, 0.0);
+      wi.h_xsx.assign(b, 0.0);
+      for (int j = 0; j < b; ++j) {
+        wi.h_xsx[j] = hd[3 * j + 1] / hd[3 * j + 2];
+        wi.h_theta[j] = hd[3 * j] / hd[3 * j + 1];
+      }
+      PP_CUDA(cudaMemcpyAsync(theta_d, wi.h_theta.data(), sizeof(double) * b, cudaMemcpyHostToDevice, s));
+      double *Dcols = c->s_D.as<double>() + (long long)off * L;
+      k_resid_dir<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, theta_d, c->diagA.as<double>(),
+                                    c->diagS.as<double>(), ov, c->opt.jacobi_floor, Dcols, rn);
+      PP_LAUNCH_CHECK("k_resid_dir");
+      std::vector<double> hr(b);
+      PP_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      wi.h_res.assign(b, 0.0);
+      for (int j = 0; j < b; ++j) {
+        double nx2 = hd[3 * j + 2];
+        wi.h_res[j] = sqrt(hr[j] / nx2) / fabs(wi.h_xsx[j]);
+      }
+      wi.order.resize(b);
+      std::iota(wi.order.begin(), wi.order.end(), 0);
+      std::stable_sort(wi.order.begin(), wi.order.end(), [&](int a, int b2) {
+        return fabs(wi.h_theta[a] - wi.shift) < fabs(wi.h_theta[b2] - wi.shift);
+      });
+      bool conv = true;
+      double worst = 0.0;
+      for (int t = 0; t < wi.nev; ++t) {
+        if (!(wi.h_res[wi.order[t]] <= tol)) conv = false;
+        worst = std::max(worst, wi.h_res[wi.order[t]]);
+      }
+      if (log_on) {
+        std::fprintf(stderr, "[pp] it %d win %d m %d b %d nev %d shift %.6f stat %d,%d worst %.2e |", it, w,
+                     m, b, wi.nev, wi.shift, hstat[0], hstat[1], worst);
+        for (int t = 0; t < wi.nev; ++t)
+          std::fprintf(stderr, " %.6f(%.1e)", wi.h_theta[wi.order[t]], wi.h_res[wi.order[t]]);
+        std::fprintf(stderr, "\n");
+      }
+      if (conv) {
+        double R = 0.0;
+        for (int t = 0; t < wi.nev; ++t) R = std::max(R, fabs(wi.h_theta[wi.order[t]] - wi.shift));
+        bool ok = true;
+        if (c->opt.select == 0) {
+          int cnt = 0;
+          for (int t = 0; t < wi.nev; ++t) {
+            double th = wi.h_theta[wi.order[t]];
+            if (th >= wi.omega0 && th <= wi.omega0 + wi.delta) ++cnt;
+          }
+          bool low_covered = (wi.shift - R <= wi.omega0);
+          bool top_covered = (wi.shift + R >= wi.omega0 + wi.delta);
+          if (!low_covered) {
+            ok = false;
+            wi.shift = std::max(wi.omega0, wi.shift - 0.5 * R);
+          } else if (cnt < wi.k && !top_covered) {
+            ok = false;
+            if (wi.nev < bcap - 2) {
+              wi.nev = std::min(wi.nev + std::max(2, wi.k / 2), bcap - 2);
+              wi.b = std::min(bcap, std::max(wi.b, wi.nev + 2));
+            } else {
+              wi.shift = wi.shift + 0.5 * R;
+            }
+          }
+          if (!ok && ++wi.adjust > 8) ok = true;  // report what has been found
+        }
+        if (ok) {
+          wi.done = true;
+          continue;
+        }
+      }
+      all_done = false;
+      wi.active.clear();
+      int nd = 0;
+      for (int j = 0; j < b; ++j) {
+        if (wi.h_res[j] <= tol) continue;
+        if (nd != j)
+          PP_CUDA(cudaMemcpyAsync(Dcols + (long long)nd * L, Dcols + (long long)j * L, vecbytes,
+                                  cudaMemcpyDeviceToDevice, s));
+        wi.active.push_back(j);
+        ++nd;
+      }
+      if (nd == 0) {
+        // every block column has converged but the window is not covered yet: widen with the
+        // next Rayleigh-Ritz vectors' residual directions on the following iteration
+        wi.b = std::min(bcap, wi.b + 2);
+      }
+      off += nd;
+    }
+    if (fail != PP_OK) break;
+    if (all_done && refine && cur_prec == PP_BF16) {
+      // refinement: restart every window on its folded targets and the next Rayleigh-Ritz
+      // vectors, recompute their products with the split (FP32-level) tensor-core sigma
+      cur_prec = PP_BF16X3;
+      tol = tol_final;
+      all_done = false;
+      for (int w = 0; w < nwin; ++w) {
+        Window &wi = W[w];
+        const int m = wi.m, b = std::min(wi.b, m);
+        const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+        PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
+        PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
+                                cudaMemcpyDeviceToDevice, s));
+        const int nout = std::min(64, std::min(m, 2 * b));
+        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept);
+        PP_LAUNCH_CHECK("k_mgs");
+        int kept = 0;
+        PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PP_CUDA(cudaStreamSynchronize(s));
+        sv.combine(wi.V, m, wi.Qk, m, kept, wi.X, 1.0, 0.0);
+        PP_CUDA(cudaMemcpyAsync(wi.V, wi.X, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+        run_sigma(kept, wi.V, wi.MV, wi.SV);
+        wi.m = kept;
+        wi.done = false;
+        wi.adjust = 0;
+      }
+      continue;
+    }
+    if (all_done) break;
+    if (off == 0) continue;
+    run_sigma(off, c->s_D.as<double>(), c->s_MD.as<double>(), c->s_SD.as<double>());
+    int pos = 0;
+    for (int w = 0; w < nwin; ++w) {
+      Window &wi = W[w];
+      if (wi.done || wi.active.empty()) continue;
+      const int nd = (int)wi.active.size();
+      const int b = std::min(wi.b, wi.m);
+      if (wi.m + nd > m_max) {
+        // thick restart: keep the folded vectors and the next Rayleigh-Ritz vectors
+        const int keep = std::min(wi.m, std::max(2 * b, m_max - nd - b));
+        const int m = wi.m;
+        const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+        PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
+        PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
+                                cudaMemcpyDeviceToDevice, s));
+        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept);
+        PP_LAUNCH_CHECK("k_mgs");
+        int kept = 0;
+        PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PP_CUDA(cudaStreamSynchronize(s));
+        // X/MX/SX hold the Ritz block that the directions were made from; stage the new
+        // basis in the direction tail (unused now) -- use X buffers after the append instead
+        double *tV = c->s_part.as<double>();
+        (void)tV;
+        double *stage = wi.X + (long long)b * L;  // room for 64 - b vectors
+        if (kept > 64 - b) kept = 64 - b;
+        sv.combine(wi.V, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+        PP_CUDA(cudaMemcpyAsync(wi.V, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+        sv.combine(wi.MV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+        PP_CUDA(cudaMemcpyAsync(wi.MV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+        sv.combine(wi.SV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+        PP_CUDA(cudaMemcpyAsync(wi.SV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+        wi.m = kept;
+      }
+      for (int t = 0; t < nd; ++t) {
+        const long long col = pos + t;
+        double *dst_v = wi.V + (long long)wi.m * L;
+        double *dst_mv = wi.MV + (long long)wi.m * L;
+        double *dst_sv = wi.SV + (long long)wi.m * L;
+        PP_CUDA(cudaMemcpyAsync(dst_v, c->s_D.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+        PP_CUDA(cudaMemcpyAsync(dst_mv, c->s_MD.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+        PP_CUDA(cudaMemcpyAsync(dst_sv, c->s_SD.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+        double *h = scratch + 512;
+        double *nrm = scratch + 512 + 2 * MAXM;
+        sv.gram(dst_v, L, 1, dst_v, L, 1, nrm + 1, 1);
+        for (int pass = 0; pass < 2; ++pass) {
+          sv.gram(wi.V, L, wi.m, dst_v, L, 1, h, 1);
+          sv.combine(wi.V, wi.m, h, wi.m, 1, dst_v, -1.0, 1.0);
+          sv.combine(wi.MV, wi.m, h, wi.m, 1, dst_mv, -1.0, 1.0);
+          sv.combine(wi.SV, wi.m, h, wi.m, 1, dst_sv, -1.0, 1.0);
+        }
+        sv.gram(dst_v, L, 1, dst_v, L, 1, nrm, 1);
+        double hn[2];
+        PP_CUDA(cudaMemcpyAsync(hn, nrm, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        PP_CUDA(cudaStreamSynchronize(s));
+        if (!(hn[0] > 1e-14 * hn[1]) || !(hn[0] > 0.0)) continue;  // dependent: drop
+        k_scale3<<<64, 256, 0, s>>>(dst_v, dst_mv, dst_sv, L, nrm);
+        PP_LAUNCH_CHECK("k_scale3");
+        wi.m += 1;
+      }
+      pos += nd;
+    }
+    c->st_iters = it + 1;
+  }
+  if (fail != PP_OK) return fail;
+
+  // ---- outputs
+  int base = 0;
+  pp_status st = PP_OK;
+  double *D = c->s_D.as<double>();
+  for (int w = 0; w < nwin; ++w) {
+    Window &wi = W[w];
+    if (!wi.done) st = PP_ENOTCONV;
+    const int nev = std::min<int>(wi.nev, (int)wi.order.size());
+    std::vector<int> sel;
+    if (c->opt.select == 1) {
+      std::vector<int> cand(wi.order.begin(), wi.order.begin() + nev);
+      std::stable_sort(cand.begin(), cand.end(), [&](int a, int b2) {
+        double da = fabs(wi.h_theta[a] - wi.omega0), db = fabs(wi.h_theta[b2] - wi.omega0);
+        return da < db || (da == db && wi.h_theta[a] < wi.h_theta[b2]);
+      });
+      for (int j = 0; j < (int)cand.size() && (int)sel.size() < wi.k; ++j) sel.push_back(cand[j]);
+    } else {
+      std::vector<int> in;
+      for (int t = 0; t < nev; ++t) {
+        int j = wi.order[t];
+        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
+      }
+      std::stable_sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
+      for (int j = 0; j < (int)in.size() && (int)sel.size() < wi.k; ++j) sel.push_back(in[j]);
+    }
+    std::stable_sort(sel.begin(), sel.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
+    const int nf = (int)sel.size();
+    nfound[w] = nf;
+    if (nf > 0) {
+      std::vector<double> th(nf), xs(nf);
+      for (int t = 0; t < nf; ++t) {
+        th[t] = wi.h_theta[sel[t]];
+        xs[t] = wi.h_xsx[sel[t]];
+        omega_out[base + t] = th[t];
+        resid_out[base + t] = wi.h_res[sel[t]];
+      }
+      // X columns are unit vectors (V orthonormal, refined coefficients normalised)
+      for (int t = 0; t < nf; ++t)
+        PP_CUDA(cudaMemcpyAsync(D + (long long)t * L, wi.X + (long long)sel[t] * L, vecbytes,
+                                cudaMemcpyDeviceToDevice, s));
+      double *thd = scratch, *xsd = scratch + 64, *od = scratch + 128;
+      PP_CUDA(cudaMemcpyAsync(thd, th.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(xsd, xs.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+      if (c->has_mu) {
+        k_osc<<<nf, 256, 0, s>>>(D, c->mu.as<double>(), ov, thd, xsd, od);
+        PP_LAUNCH_CHECK("k_osc");
+        PP_CUDA(cudaMemcpyAsync(osc_out + base, od, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+      } else {
+        for (int t = 0; t < nf; ++t) osc_out[base + t] = 0.0;
+      }
+      if (vecs_out) {
+        PP_CUDA(cudaMemcpyAsync(vecs_out + (long long)base * L, D, vecbytes * nf, cudaMemcpyDeviceToHost, s));
+        PP_CUDA(cudaStreamSynchronize(s));
+        for (int t = 0; t < nf; ++t) {
+          double sc = 1.0 / sqrt(fabs(xs[t]));
+          double *vv = vecs_out + (long long)(base + t) * L;
+          for (long long l = 0; l < L; ++l) vv[l] *= sc;
+        }
+      }
+    }
+    PP_CUDA(cudaStreamSynchronize(s));
+    base += wi.k;
+  }
+  return st;
+}

@@ -1,0 +1,704 @@
+// Tensor-core (tcgen05 / TMA / TMEM, sm_103a) form of the sigma product.
+//
+// Dominant contraction of Sec. 2.2's B(2) (and its ring/ladder parts):
+//   P[(i,c), n] = sum_(j,d) t_ij^cd  C[n, (j,d)],   C = C_Q(V) for every (V, Q).
+// The amplitudes are regenerated slab by slab on the tensor cores,
+//   t_ij^cd = (sum_Q B_Qic B_Qjd - sum_Q B_Qjc B_Qid) / (e_i + e_j - e_c - e_d),
+// with both products accumulated in TMEM by one CTA and combined in the
+// epilogue (BF16 out), then consumed by a long-K BF16 GEMM whose FP32
+// accumulator lives in TMEM.  Only one slab of t (a few occupied indices) is
+// alive at any time, in an L2-sized staging buffer; t is never stored whole.
+// Split-BF16 ("bf16x3") operands give FP32-level products for the refinement.
+//
+// Kernel structure (both kernels): 128 threads; warp 0 lane 0 issues TMA loads
+// into a STAGES-deep ring of 128B-swizzled shared tiles, warp 1 lane 0 issues
+// tcgen05.mma (M = 128, K = 16 per instruction) and commits each stage back to
+// the producer; all four warps read the accumulator out of TMEM (tcgen05.ld,
+// 32 lanes per warp).  Every mbarrier wait is bounded: on timeout the kernel
+// raises an error flag, stops issuing, frees its TMEM and returns.
+#include "pp_internal.h"
+#include "sigma_terms.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// device helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bounded wait on the given phase parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(const void *p) {
+  const uint64_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (a >> 4) & 0x3FFFull;           // start address
+  d |= (uint64_t)(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= 1ull << 46;                     // descriptor version
+  d |= 2ull << 61;                     // 128B swizzle
+  return d;
+}
+// instruction descriptor: kind::f16, A/B BF16, D FP32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int BM = 128, BK = 64;  // BK bf16 = 128 bytes = one swizzle atom row
+
+// ---------------------------------------------------------------------------
+// generic GEMM: C[M x N] (+)= alpha * sum_seg A_seg[M x K] B_seg[N x K]^T
+// (A and B BF16 K-major via TMA; C FP32 row-major with leading dimension ldc)
+// ---------------------------------------------------------------------------
+struct alignas(64) GemmMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+struct GemmArgs {
+  int M, N, nk, nseg;
+  float alpha;
+  int accumulate;
+  float *C;
+  long long ldc;
+  int *err;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ GemmMaps maps, GemmArgs args) {
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int total = args.nseg * args.nk;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
+        atomicExch(args.err, 1);
+        abort_flag = 1;
+        break;
+      }
+      const int seg = kb / args.nk, k = kb % args.nk;
+      uint8_t *sa = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      tma_load_2d(sa, &maps.a[seg], k * BK, m0, &full_bar[s]);
+      tma_load_2d(sa + A_BYTES, &maps.b[seg], k * BK, n0, &full_bar[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&full_bar[s], ph)) {
+        atomicExch(args.err, 2);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      uint8_t *sa = smem + s * STAGE_BYTES;
+      const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&acc_bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&acc_bar, 0);
+  if (!ok && lane == 0) atomicExch(args.err, 3);
+  tc_fence_after();
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tmem_ld32(trow + c0, v);
+      if (row < args.M) {
+        float *cp = args.C + (long long)row * args.ldc + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (n0 + c0 + j < args.N) {
+            float x = args.alpha * v[j];
+            if (args.accumulate) x += cp[j];
+            cp[j] = x;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// ---------------------------------------------------------------------------
+// amplitude slab: T[(ii, c)][j*v + d] = t_{i j}^{c d}, i = i0 + ii, for c, d in 128-wide
+// tiles.  Two accumulators: D1 = B_i[ct]^T B_j[dt], D2 = B_j[ct]^T B_i[dt], K = Q (padded).
+// The TMA source is BovT[(i,c)][Q] (BF16, row stride ldq).
+// ---------------------------------------------------------------------------
+struct alignas(64) TgenMaps {
+  CUtensorMap hi, lo;
+};
+struct TgenArgs {
+  int o, v, nk, i0, ntile, nseg;  // ntile = ceil(v / 128); nseg 1 (hi.hi) or 3 (+ hi.lo + lo.hi)
+  const double *eps;
+  __nv_bfloat16 *Thi, *Tlo;  // Tlo may be null
+  long long ldT;
+  int *err;
+};
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMaps maps, TgenArgs args) {
+  constexpr uint32_t TILE = BM * BK * 2, STAGE_BYTES = 4 * TILE;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ct = blockIdx.x / args.ntile, dt = blockIdx.x % args.ntile;
+  const int j = blockIdx.y, ii = blockIdx.z, i = args.i0 + ii;
+  const int v = args.v;
+  const int c0 = ct * BM, d0 = dt * BM;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int total = args.nk * args.nseg;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
+        atomicExch(args.err, 11);
+        break;
+      }
+      // segment 0: hi x hi, 1: hi x lo, 2: lo x hi
+      const int seg = kb / args.nk;
+      const CUtensorMap *ma = (seg == 2) ? &maps.lo : &maps.hi;
+      const CUtensorMap *mb = (seg == 1) ? &maps.lo : &maps.hi;
+      uint8_t *sa = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      const int x = (kb % args.nk) * BK;
+      tma_load_2d(sa, ma, x, i * v + c0, &full_bar[s]);             // A1 = B_i[ct]
+      tma_load_2d(sa + TILE, mb, x, j * v + d0, &full_bar[s]);      // B1 = B_j[dt]
+      tma_load_2d(sa + 2 * TILE, ma, x, j * v + c0, &full_bar[s]);  // A2 = B_j[ct]
+      tma_load_2d(sa + 3 * TILE, mb, x, i * v + d0, &full_bar[s]);  // B2 = B_i[dt]
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BM);
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&full_bar[s], ph)) {
+        atomicExch(args.err, 12);
+        break;
+      }
+      tc_fence_after();
+      uint8_t *sa = smem + s * STAGE_BYTES;
+      const uint64_t a1 = sdesc(sa), b1 = sdesc(sa + TILE), a2 = sdesc(sa + 2 * TILE), b2 = sdesc(sa + 3 * TILE);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        mma_bf16(tmem, a1 + 2 * k, b1 + 2 * k, idesc, acc);
+        mma_bf16(tmem + BM, a2 + 2 * k, b2 + 2 * k, idesc, acc);
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&acc_bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&acc_bar, 0);
+  if (!ok && lane == 0) atomicExch(args.err, 13);
+  tc_fence_after();
+  if (ok) {
+    const int c = c0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const int o = args.o;
+    const double eij_c = (c < v) ? args.eps[i] + args.eps[j] - args.eps[o + c] : 0.0;
+    __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + c) * args.ldT + (long long)j * v;
+    __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + c) * args.ldT + (long long)j * v : nullptr;
+    for (int cc = 0; cc < BM; cc += 32) {
+      float d1[32], d2[32];
+      tmem_ld32(trow + cc, d1);
+      tmem_ld32(trow + BM + cc, d2);
+      if (c < v) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int d = d0 + cc + q;
+          if (d < v) {
+            const float t = (d1[q] - d2[q]) / (float)(eij_c - args.eps[o + d]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(t);
+            hrow[d] = h;
+            if (lrow) lrow[d] = __float2bfloat16_rn(t - __bfloat162float(h));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+// dst[r][k] (row stride ldd, zero for k >= ncol) = bf16 hi (or lo remainder) of src[r][k]
+template <class S>
+__global__ void k_to_bf16(const S *__restrict__ src, long long rows, long long ncol, long long lds,
+                          __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo, long long ldd) {
+  const long long total = rows * ldd;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    long long r = p / ldd, k = p % ldd;
+    float x = (k < ncol) ? (float)src[r * lds + k] : 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    if (lo) lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+// BovT[(i,a)][Q] (row stride ldq, zero padded) from Bov[Q][i][a] (double)
+__global__ void k_bovT(const double *__restrict__ Bov, int Q, long long ov, __nv_bfloat16 *__restrict__ hi,
+                       __nv_bfloat16 *__restrict__ lo, long long ldq) {
+  const long long total = ov * ldq;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    long long ia = p / ldq, q = p % ldq;
+    float x = (q < Q) ? (float)Bov[q * ov + ia] : 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    if (lo) lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+__global__ void k_d2f(const double *__restrict__ s, float *__restrict__ d, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    d[p] = (float)s[p];
+}
+
+inline dim3 grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return dim3((unsigned)b);
+}
+
+// ---------------------------------------------------------------------------
+// host: tensor maps via the driver entry point (no link-time libcuda dependency)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    PP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw PPError(PP_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+// rows x K bf16 matrix, K contiguous with row stride ld (elements); box 64 x box_rows
+static CUtensorMap kmajor_map(const void *base, long long K, long long rows, long long ld, int box_rows) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15) || (K % BK))
+    throw PPError(PP_EINVAL, "tensor map: base, stride or K not aligned");
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw PPError(PP_ECUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+constexpr int GEMM_BN = 256, GEMM_STAGES = 4, TGEN_STAGES = 3;
+constexpr size_t gemm_smem() { return (size_t)GEMM_STAGES * (BM * BK * 2 + GEMM_BN * BK * 2) + 1024; }
+constexpr size_t tgen_smem() { return (size_t)TGEN_STAGES * 4 * BM * BK * 2 + 1024; }
+
+// C (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K
+void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *A, long long lda,
+               const __nv_bfloat16 *const *B, long long ldb, float *C, long long ldc, float alpha, bool accumulate,
+               int *err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_smem()));
+    attr = true;
+  }
+  GemmMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int g = 0; g < nseg; ++g) {
+    maps.a[g] = kmajor_map(A[g], K, M, lda, BM);
+    maps.b[g] = kmajor_map(B[g], K, N, ldb, GEMM_BN);
+  }
+  GemmArgs a{M, N, (int)(K / BK), nseg, alpha, accumulate ? 1 : 0, C, ldc, err};
+  dim3 grid((N + GEMM_BN - 1) / GEMM_BN, (M + BM - 1) / BM);
+  k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
+  PP_LAUNCH_CHECK("k_gemm_bf16");
+}
+
+void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq, long long ov, int o, int v,
+          int i0, int ni, const double *eps, __nv_bfloat16 *Thi, __nv_bfloat16 *Tlo, long long ldT, int *err,
+          cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    PP_CUDA(cudaFuncSetAttribute(k_tgen<TGEN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tgen_smem()));
+    attr = true;
+  }
+  TgenMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  maps.hi = kmajor_map(bovT, ldq, ov, ldq, BM);
+  maps.lo = bovT_lo ? kmajor_map(bovT_lo, ldq, ov, ldq, BM) : maps.hi;
+  const int nt = (v + BM - 1) / BM;
+  TgenArgs a{o, v, (int)(ldq / BK), i0, nt, bovT_lo ? 3 : 1, eps, Thi, Tlo, ldT, err};
+  dim3 grid(nt * nt, o, ni);
+  k_tgen<TGEN_STAGES><<<grid, 128, tgen_smem(), s>>>(maps, a);
+  PP_LAUNCH_CHECK("k_tgen");
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// plan: BF16 / FP32 resident copies and workspaces of the tensor-core form
+// ---------------------------------------------------------------------------
+// per-kernel launch timing of the tensor-core form (enabled by pp_profile)
+struct KernelProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev[2];  // start/stop pairs per kernel id
+  long long launches[2] = {0, 0};
+  double flops[2] = {0, 0};
+  double ms[2] = {0, 0};
+};
+struct TcPlan {
+  long long ldq = 0, ldT = 0;
+  KernelProfile prof;
+  int slab_i = 1, Rmax = 2;
+  DevBuf bovT_hi, bovT_lo;                     // [ov][ldq]
+  DevBuf f_gap, f_eps, f_Bov, f_Boo, f_Bvv, f_BvvP, f_BooT, f_GB, f_Gam, f_poo, f_qoo, f_pvv, f_qvv;
+  DevBuf w_V, w_acc, w_tmp, w_cq, w_W, w_U, w_EF, w_P;
+  DevBuf c_hi, c_lo;                           // C_Q(V) in BF16 [R*Q][ldT]
+  DevBuf t_hi, t_lo;                           // amplitude slab [slab rows][ldT]
+  DevBuf err;
+};
+
+void tc_destroy(pp_ctx *c) {
+  if (!c->tc) return;
+  TcPlan *p = c->tc;
+  DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->f_gap, &p->f_eps, &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP,
+                    &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo, &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V,
+                    &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W, &p->w_U, &p->w_EF, &p->w_P, &p->c_hi,
+                    &p->c_lo, &p->t_hi, &p->t_lo, &p->err};
+  for (DevBuf *b : bufs) b->release();
+  for (auto &v : p->prof.ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  delete p;
+  c->tc = nullptr;
+}
+
+static void prof_mark(KernelProfile &pr, int id, cudaStream_t s) {
+  if (!pr.on) return;
+  cudaEvent_t e;
+  PP_CUDA(cudaEventCreate(&e));
+  PP_CUDA(cudaEventRecord(e, s));
+  pr.ev[id].push_back(e);
+}
+// fold recorded event pairs into the totals (synchronises on the last event)
+static void prof_collect(KernelProfile &pr) {
+  for (int id = 0; id < 2; ++id) {
+    auto &v = pr.ev[id];
+    for (size_t k = 0; k + 1 < v.size(); k += 2) {
+      PP_CUDA(cudaEventSynchronize(v[k + 1]));
+      float ms = 0.f;
+      PP_CUDA(cudaEventElapsedTime(&ms, v[k], v[k + 1]));
+      pr.ms[id] += ms;
+      cudaEventDestroy(v[k]);
+      cudaEventDestroy(v[k + 1]);
+    }
+    v.clear();
+  }
+}
+
+static void f32_copy(DevBuf &dst, const DevBuf &src, long long n, cudaStream_t s) {
+  dst.ensure(sizeof(float) * (size_t)std::max<long long>(n, 1));
+  if (n > 0) {
+    tc::k_d2f<<<tc::grid_for(n), 256, 0, s>>>(src.as<double>(), dst.as<float>(), n);
+    PP_LAUNCH_CHECK("k_d2f");
+  }
+}
+
+static TcPlan *tc_plan(pp_ctx *c) {
+  if (c->tc) return c->tc;
+  TcPlan *p = new TcPlan();
+  c->tc = p;
+  const long long o = c->o, v = c->v, Q = c->Q, ov = c->ov;
+  cudaStream_t s = c->stream;
+  p->ldq = std::max<long long>(tc::BK, ((Q + tc::BK - 1) / tc::BK) * tc::BK);
+  p->ldT = ((ov + tc::BK - 1) / tc::BK) * tc::BK;
+  // resident FP32 copies of the small-term operands
+  f32_copy(p->f_gap, c->gap, ov, s);
+  f32_copy(p->f_eps, c->eps, c->n, s);
+  f32_copy(p->f_Bov, c->Bov, Q * ov, s);
+  f32_copy(p->f_Boo, c->Boo, Q * o * o, s);
+  f32_copy(p->f_Bvv, c->Bvv, Q * v * v, s);
+  f32_copy(p->f_BvvP, c->BvvP, Q * v * v, s);
+  f32_copy(p->f_BooT, c->BooT, Q * o * o, s);
+  f32_copy(p->f_GB, c->GB, 2 * Q * ov, s);
+  f32_copy(p->f_Gam, c->Gam, Q * ov, s);
+  f32_copy(p->f_poo, c->p_oo, o * o, s);
+  f32_copy(p->f_qoo, c->q_oo, o * o, s);
+  f32_copy(p->f_pvv, c->p_vv, v * v, s);
+  f32_copy(p->f_qvv, c->q_vv, v * v, s);
+  if (c->opt.order >= 2) {
+    p->bovT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
+    p->bovT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
+    tc::k_bovT<<<tc::grid_for(ov * p->ldq), 256, 0, s>>>(c->Bov.as<double>(), (int)Q, ov,
+                                                         p->bovT_hi.as<__nv_bfloat16>(),
+                                                         p->bovT_lo.as<__nv_bfloat16>(), p->ldq);
+    PP_LAUNCH_CHECK("k_bovT");
+  }
+  // workspaces: R half-vectors per chunk; the amplitude slab keeps ~64 MB of BF16
+  const long long per_half = 3 * Q * ov + 2 * Q * o * o + 8 * ov + Q;
+  long long R = (8LL << 30) / (4 * per_half + 4 * Q * p->ldT);
+  R = std::max<long long>(2, std::min<long long>(R, 64));
+  R &= ~1LL;
+  p->Rmax = (int)R;
+  const long long si = std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
+  p->slab_i = (int)si;
+  p->err.ensure(sizeof(int) * 4);
+  PP_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int) * 4, s));
+  return p;
+}
+
+// BF16 tensor-core sigma: small terms in FP32, amplitude contraction on tcgen05.
+// split = true uses hi/lo BF16 pairs (three products) for an FP32-level result.
+void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split) {
+  TcPlan *p = tc_plan(c);
+  const int o = c->o, v = c->v, Q = c->Q;
+  const long long ov = c->ov;
+  cudaStream_t s = c->stream;
+  const int Rmax = p->Rmax;
+  p->w_V.ensure(sizeof(float) * (size_t)Rmax * ov);
+  p->w_acc.ensure(sizeof(float) * 2 * (size_t)Rmax * ov);
+  p->w_tmp.ensure(sizeof(float) * 4 * (size_t)Rmax * ov);
+  if (c->opt.order >= 1) {
+    p->w_cq.ensure(sizeof(float) * (size_t)Q * Rmax);
+    p->w_W.ensure(sizeof(float) * (size_t)Rmax * o * Q * v);
+    p->w_EF.ensure(sizeof(float) * (size_t)Rmax * 2 * Q * o * o);
+  }
+  if (c->opt.order >= 2) {
+    p->w_U.ensure(sizeof(float) * (size_t)Rmax * Q * ov);
+    p->w_P.ensure(sizeof(float) * (size_t)Rmax * Q * ov);
+    p->c_hi.ensure(sizeof(__nv_bfloat16) * (size_t)Rmax * Q * p->ldT);
+    if (split) p->c_lo.ensure(sizeof(__nv_bfloat16) * (size_t)Rmax * Q * p->ldT);
+    p->t_hi.ensure(sizeof(__nv_bfloat16) * (size_t)p->slab_i * v * p->ldT);
+    if (split) p->t_lo.ensure(sizeof(__nv_bfloat16) * (size_t)p->slab_i * v * p->ldT);
+  }
+  SigmaRes<float> res{p->f_gap.as<float>(), p->f_eps.as<float>(), p->f_Bov.as<float>(), p->f_Boo.as<float>(),
+                      p->f_Bvv.as<float>(), p->f_BvvP.as<float>(), p->f_BooT.as<float>(), p->f_GB.as<float>(),
+                      p->f_Gam.as<float>(), p->f_poo.as<float>(), p->f_qoo.as<float>(), p->f_pvv.as<float>(),
+                      p->f_qvv.as<float>()};
+  int *err = p->err.as<int>();
+  const int R_total = 2 * nvec;
+  for (int r0 = 0; r0 < R_total; r0 += Rmax) {
+    const int R = std::min(Rmax, R_total - r0);
+    const double *V64 = Zd + (long long)r0 * ov;
+    float *V = p->w_V.as<float>();
+    tc::k_d2f<<<tc::grid_for((long long)R * ov), 256, 0, s>>>(V64, V, (long long)R * ov);
+    PP_LAUNCH_CHECK("k_d2f");
+    SigmaWork<float> wk{p->w_acc.as<float>(), p->w_acc.as<float>() + (long long)R * ov, p->w_tmp.as<float>(),
+                        p->w_cq.as<float>(), p->w_W.as<float>(), p->w_U.as<float>(), p->w_EF.as<float>()};
+    auto ladder = [&](int Rc, const float *Cmat, float *P) -> PLayout {
+      const long long NC = (long long)Rc * Q;
+      __nv_bfloat16 *chi = p->c_hi.as<__nv_bfloat16>();
+      __nv_bfloat16 *clo = split ? p->c_lo.as<__nv_bfloat16>() : nullptr;
+      tc::k_to_bf16<float><<<tc::grid_for(NC * p->ldT), 256, 0, s>>>(Cmat, NC, ov, ov, chi, clo, p->ldT);
+      PP_LAUNCH_CHECK("k_to_bf16");
+      __nv_bfloat16 *thi = p->t_hi.as<__nv_bfloat16>();
+      __nv_bfloat16 *tlo = split ? p->t_lo.as<__nv_bfloat16>() : nullptr;
+      const int si = p->slab_i;
+      for (int i0 = 0; i0 < o; i0 += si) {
+        const int ni = std::min(si, o - i0);
+        const long long rows = (long long)ni * v;
+        if (p->ldT > ov) {  // zero the K padding of the slab rows
+          PP_CUDA(cudaMemset2DAsync(thi + ov, p->ldT * 2, 0, (p->ldT - ov) * 2, rows, s));
+          if (tlo) PP_CUDA(cudaMemset2DAsync(tlo + ov, p->ldT * 2, 0, (p->ldT - ov) * 2, rows, s));
+        }
+        prof_mark(p->prof, 1, s);
+        tc::tgen(p->bovT_hi.as<__nv_bfloat16>(), split ? p->bovT_lo.as<__nv_bfloat16>() : nullptr, p->ldq, ov, o,
+                 v, i0, ni, c->eps.as<double>(), thi, tlo, p->ldT, err, s);
+        prof_mark(p->prof, 1, s);
+        if (p->prof.on) {
+          p->prof.launches[1] += 1;
+          p->prof.flops[1] += 2.0 * 2.0 * (double)Q * (double)rows * (double)ov * (split ? 3 : 1);
+        }
+        // P rows (i,c) of this slab: P[(i,c)][(r,Q)] (row stride NC)
+        const __nv_bfloat16 *A[3] = {thi, thi, tlo};
+        const __nv_bfloat16 *B[3] = {chi, clo, chi};
+        prof_mark(p->prof, 0, s);
+        tc::gemm_bf16((int)rows, (int)NC, p->ldT, split ? 3 : 1, A, p->ldT, B, p->ldT,
+                      P + (long long)i0 * v * NC, NC, 1.0f, false, err, s);
+        prof_mark(p->prof, 0, s);
+        if (p->prof.on) {
+          p->prof.launches[0] += 1;
+          p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov * (split ? 3 : 1);
+        }
+      }
+      return PLayout{(long long)Q, NC};
+    };
+    sigma_chunk<float>(c, R, V, V64, sig_d + (long long)r0 * ov, met_d ? met_d + (long long)r0 * ov : nullptr,
+                       res, wk, p->w_P.as<float>(), ladder);
+  }
+  int herr = 0;
+  PP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    PP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    throw PPError(PP_ETIMEOUT, "tensor-core kernel wait timed out (code " + std::to_string(herr) + ")");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// profiling entry points (C ABI)
+// ---------------------------------------------------------------------------
+extern "C" pp_status pp_profile(pp_ctx *c, int enable) {
+  if (!c) return PP_EINVAL;
+  try {
+    TcPlan *p = tc_plan(c);
+    prof_collect(p->prof);
+    p->prof.on = enable != 0;
+    if (enable)
+      for (int id = 0; id < 2; ++id) {
+        p->prof.launches[id] = 0;
+        p->prof.flops[id] = 0;
+        p->prof.ms[id] = 0;
+      }
+    return PP_OK;
+  } catch (const PPError &e) {
+    c->err = e.msg;
+    return e.st;
+  }
+}
+
+extern "C" pp_status pp_profile_read(pp_ctx *c, int id, long long *launches, double *ms, double *flops) {
+  if (!c || id < 0 || id > 1) return PP_EINVAL;
+  try {
+    TcPlan *p = tc_plan(c);
+    prof_collect(p->prof);
+    if (launches) *launches = p->prof.launches[id];
+    if (ms) *ms = p->prof.ms[id];
+    if (flops) *flops = p->prof.flops[id];
+    return PP_OK;
+  } catch (const PPError &e) {
+    c->err = e.msg;
+    return e.st;
+  }
+}

@@ -10,5 +10,7 @@ from .inputs import (  # noqa: F401
     CONFIGS,
     make_inputs,
     scaled_sigma_b,
+    perturbative_sigma_b,
+    random_vectors,
     window_start,
 )

@@ -13,13 +13,18 @@ synthetic ones with the shapes of Table 1's particle-hole spaces:
 
 Draw order is eps_occ, eps_vir, B, mu from ``numpy.random.default_rng(seed)``.
 
-Two widths of B are offered.  ``literal`` uses sigma_B = 0.05 at every size.
+Three widths of B are offered.  ``literal`` uses sigma_B = 0.05 at every size.
 ``scaled`` shrinks sigma_B with the dot so that the second-order density
 correction and the first-order coupling stay at the level of the 8/24/64
 case: sigma_B = 0.05 * (8 * 24**2 * 64 / (o * v**2 * Q)) ** 0.25.  With the
 literal width the perturbation grows with the dot until the metric S stops
-being positive definite, so root finding above the tiny case uses ``scaled``;
-sigma products and FLOP counts do not depend on the width.
+being positive definite.  ``perturbative`` keeps instead the first-order
+coupling per matrix element, sigma_B^2 sqrt(Q), in a fixed ratio to the mean
+level spacing of the ov gaps: sigma_B = 0.82 / sqrt(o v sqrt(Q)).  There the
+second-order metric stays within a few per cent of 1 and each interior root
+mixes a handful of particle-hole states, the regime in which a diagonal Jacobi
+splitting is a useful preconditioner; root finding above the tiny case uses it.
+Sigma products and FLOP counts do not depend on the width.
 """
 
 from __future__ import annotations
@@ -61,6 +66,10 @@ def scaled_sigma_b(nocc: int, nvir: int, naux: int) -> float:
     return SIGMA_B_LITERAL * (8 * 24 ** 2 * 64 / (nocc * nvir ** 2 * naux)) ** 0.25
 
 
+def perturbative_sigma_b(nocc: int, nvir: int, naux: int) -> float:
+    return 0.82 / float(np.sqrt(nocc * nvir * np.sqrt(max(naux, 1))))
+
+
 def make_inputs(nocc: int, nvir: int, naux: int, seed: int, mode: str = "literal",
                 sigma_b: float | None = None, b_dtype=np.float64) -> DotInputs:
     """Draw one synthetic dot.  ``mode`` is 'literal', 'scaled' or 'zero' (B = 0)."""
@@ -71,6 +80,8 @@ def make_inputs(nocc: int, nvir: int, naux: int, seed: int, mode: str = "literal
             sigma_b = SIGMA_B_LITERAL
         elif mode == "scaled":
             sigma_b = scaled_sigma_b(nocc, nvir, naux)
+        elif mode == "perturbative":
+            sigma_b = perturbative_sigma_b(nocc, nvir, naux)
         else:
             raise ValueError(f"unknown mode {mode!r}")
     rng = np.random.default_rng(seed)
