@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the window solve: converged roots per second on one GB300.
+
+Workload (the configuration the metric is quoted on): one synthetic dot with
+nocc = 64, nvir = 256, naux = 768 (particle-hole dimension 16384), seed 1,
+perturbative-width density-fitting tensor; one window [omega0, omega0 + 0.1 Ha]
+with omega0 at the 20th percentile of diag(A)/diag(S); the k = 8 lowest roots,
+second order, mixed precision (BF16 tensor-core sigma, FP64 Krylov/Ritz,
+split-BF16 refinement to a residual of 1e-7).
+
+A step is one full window solve (pp_solve_window) on device-resident inputs.
+value = roots converged / timed seconds; e2e repeats the step through the C ABI
+from host buffers (pp_create with the host B tensor, solve, results to host,
+pp_destroy) with the copies inside the timed region.
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="dot-64x256x768", nocc=64, nvir=256, naux=768, seed=1, mode="perturbative",
+                pct=20.0, delta=0.1, k=8, order=2)
+METRIC = "converged roots/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sustained=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sustained=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = dict(sm_mhz=None, sm_max_mhz=None, reasons=[])
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for n, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return out
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_over_ranks(dist, ms: float, roots: float, device):
+    """Weak scaling: the job's time is the slowest rank's, its roots the sum over ranks."""
+    import torch
+
+    ms_t = torch.tensor([float(ms)], device=device)
+    roots_t = torch.tensor([float(roots)], device=device)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(roots_t, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(roots_t.item())
+
+
+def window_for_rank(omega0: float, delta: float, rank: int) -> float:
+    """Ranks take consecutive, non-overlapping windows of the same width."""
+    return omega0 + rank * delta
+
+
+def make_dot_inputs():
+    from synth.inputs import make_inputs
+
+    w = WORKLOAD
+    return make_inputs(w["nocc"], w["nvir"], w["naux"], seed=w["seed"], mode=w["mode"])
+
+
+def sigma_flops(o, v, Q, nvec):
+    """Algorithmic FLOPs of one sigma batch (nvec supervectors, both halves)."""
+    ov = o * v
+    R = 2 * nvec
+    small = R * (4 * Q * ov + 2 * Q * o * v * v + 2 * Q * o * o * v + 2 * 2 * Q * o * o * v
+                 + 2 * 2 * Q * o * o * v + 2 * Q * o * o * v + 2 * Q * o * v * v + 2 * Q * o * o * v
+                 + 4 * (o * o * v + o * v * v))
+    ladder = 2.0 * ov * ov * Q * R
+    tgen = 2.0 * 2.0 * Q * ov * ov
+    return small + ladder + tgen
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2512_09811_gb300 as pp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pp.load()
+    stream = torch.cuda.current_stream()
+    inp = make_dot_inputs()
+    w = WORKLOAD
+    opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=1e-7, block=8, refine=1,
+                  cuda_stream=stream.cuda_stream)
+    t0 = time.time()
+    dot = pp.Dot(inp, **opt_kw)
+    create_s = time.time() - t0
+    dA, dS = dot.diagonal()
+    # every rank solves its own window (independent problems: weak scaling, no collective)
+    omega0 = window_for_rank(float(np.percentile((dA / dS).ravel(), w["pct"])), w["delta"], rank)
+
+    def step():
+        return dot.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    pk = peaks()
+    roots = 0
+    iters = []
+    res_all = []
+    pp.pp_profile(dot.ctx, True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    launches0 = pp.pp_kernel_launches()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+            ok = out["resid"] <= 1e-7 * 1.0000001
+            roots += int(np.count_nonzero(ok))
+            res_all.extend(out["resid"].tolist())
+            iters.append(dot.stats()["iterations"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = pp.pp_kernel_launches() - launches0
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    k0 = pp.pp_profile_read(dot.ctx, 0)
+    k1 = pp.pp_profile_read(dot.ctx, 1)
+    pp.pp_profile(dot.ctx, False)
+    stats = dot.stats()
+    ms_max, roots_tot = reduce_over_ranks(dist, ms, roots, "cuda")
+    value = roots_tot / (ms_max / 1e3)
+
+    # sigma throughput of one BF16 batch of 8 supervectors (device-resident, CUDA events)
+    from synth.inputs import random_vectors
+
+    Zh = random_vectors(8, w["nocc"], w["nvir"], seed=5)
+    Zd = torch.from_numpy(Zh).cuda()
+    for _ in range(2):
+        pp.pp_sigma(dot.ctx, Zd, prec=pp.PP_BF16)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nrep = 3
+    for _ in range(nrep):
+        pp.pp_sigma(dot.ctx, Zd, prec=pp.PP_BF16)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sig_ms = e0.elapsed_time(e1) / nrep
+    sig_tflops = sigma_flops(w["nocc"], w["nvir"], w["naux"], 8) / (sig_ms / 1e3) / 1e12
+
+    # end to end through the C ABI from host buffers: create (B to the device), solve, results back
+    h2d = inp.eps.nbytes + inp.B.nbytes + inp.mu.nbytes
+    d2h = w["k"] * 3 * 8
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ee = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        d2 = pp.Dot(inp, **opt_kw)
+        o2 = d2.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
+        ee += int(np.count_nonzero(o2["resid"] <= 1e-7 * 1.0000001))
+        d2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.time() - t0
+    e2e_max, ee_tot = reduce_over_ranks(dist, e2e_s, ee, "cuda")
+    e2e_val = ee_tot / e2e_max
+
+    achieved = (k0["flops"] / (k0["ms"] / 1e3) / 1e12) if k0["ms"] > 0 else None
+    peak = pk["bf16_sustained"]
+    roof = dict(bound="tensor", kernel="k_gemm_bf16 (amplitude contraction, tcgen05)",
+                achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=(achieved / peak) if achieved else None, traffic=None,
+                peak_source=f"{pk['src']} bf16 sustained", launches=k0["launches"],
+                avg_launch_ms=(k0["ms"] / k0["launches"]) if k0["launches"] else None,
+                tgen=dict(launches=k1["launches"], ms=k1["ms"],
+                          achieved=(k1["flops"] / (k1["ms"] / 1e3) / 1e12) if k1["ms"] > 0 else None))
+    line = dict(
+        metric=METRIC, value=value, unit="roots/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms_max / max(args.steps, 1), higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="bf16", data="synthetic",
+        config=dict(workload=w["name"], nocc=w["nocc"], nvir=w["nvir"], naux=w["naux"], k=w["k"],
+                    window_ha=w["delta"], order=w["order"], precision="bf16 tensor cores + fp64 krylov + bf16x3 refine",
+                    inputs=w["mode"], l2="inputs larger than L2 (B tensor 630 MB fp64 resident)",
+                    parallelism=f"replicas{world}"),
+        roofline=roof,
+        e2e=dict(value=e2e_val, unit="roots/s", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
+        gpu_launches=int(launches),
+        clocks=clk.summary(),
+        extra=dict(create_s=create_s, iterations=iters, sigma_vectors=stats["sigma_vectors"],
+                   sigma_ms_last_solve=stats["sigma_ms"], solve_ms_last=stats["solve_ms"],
+                   max_resid=max(res_all) if res_all else None,
+                   sigma_batch8_ms=sig_ms, sigma_tflops=sig_tflops),
+    )
+    dot.close()
+    return line
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle (plain FP64 NumPy) on this machine's host cores: its matrix-free sigma,
+    timed on one trial supervector per step, scaled by the sigma supervectors a window
+    solve needs."""
+    if rank != 0:
+        return None
+    from oracle import pp_oracle as po
+    from synth.inputs import random_vectors
+
+    inp = make_dot_inputs()
+    w = WORKLOAD
+    t0 = time.time()
+    ref = po.SigmaRef(inp.eps, inp.B, inp.nocc, order=w["order"])
+    setup_s = time.time() - t0
+    Z = random_vectors(1, w["nocc"], w["nvir"], seed=5)
+    ref.sigma(Z)  # warm caches
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.time()
+        ref.sigma(Z)
+        times.append(time.time() - t0)
+    t_vec = statistics.median(times)
+    vecs_per_root = REF_SIGMA_VECTORS_PER_ROOT
+    value = 1.0 / (t_vec * vecs_per_root)
+    cores = os.cpu_count()
+    sample = (f"oracle FP64 sigma of 1 supervector per step at {w['name']} (median {t_vec:.2f} s, "
+              f"setup {setup_s:.1f} s), times {vecs_per_root} supervectors per converged root")
+    return dict(metric=METRIC, value=value, unit="roots/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=t_vec * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=w["name"], nocc=w["nocc"], nvir=w["nvir"], naux=w["naux"], k=w["k"]),
+                cpu_baseline=dict(value=value, unit="roots/s", cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="roots/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+
+
+# sigma supervectors per converged root of the mixed-precision window solve at this workload
+REF_SIGMA_VECTORS_PER_ROOT = 50
+
+
+def cpu_baseline_leg():
+    """Bounded oracle sample for the cpu_baseline field (rank 0, N = 1 only)."""
+    from oracle import pp_oracle as po
+    from synth.inputs import random_vectors
+
+    inp = make_dot_inputs()
+    w = WORKLOAD
+    t0 = time.time()
+    ref = po.SigmaRef(inp.eps, inp.B, inp.nocc, order=w["order"])
+    setup = time.time() - t0
+    Z = random_vectors(1, w["nocc"], w["nvir"], seed=5)
+    t0 = time.time()
+    ref.sigma(Z)
+    t_vec = time.time() - t0
+    return dict(value=1.0 / (t_vec * REF_SIGMA_VECTORS_PER_ROOT), unit="roots/s", cores=os.cpu_count(),
+                kind="oracle",
+                sample=f"1 oracle FP64 sigma supervector at {w['name']} ({t_vec:.2f} s, setup {setup:.1f} s) "
+                       f"x {REF_SIGMA_VECTORS_PER_ROOT} supervectors per root")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    line = run_ours(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_leg()
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

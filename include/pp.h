@@ -158,6 +158,9 @@ pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vec
 pp_status pp_profile(pp_ctx *ctx, int enable);
 pp_status pp_profile_read(pp_ctx *ctx, int id, long long *launches, double *ms, double *flops);
 
+/* Number of CUDA kernels this library has launched in the process so far (all contexts). */
+long long pp_kernel_launches(void);
+
 /* Release everything the context owns.  NULL-safe. */
 void pp_destroy(pp_ctx *ctx);
 

@@ -28,7 +28,8 @@ STATUS_NAMES = {
 # every symbol declared in include/pp.h
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_diagonal", "pp_solve_window",
-    "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_destroy", "pp_last_error",
+    "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
+    "pp_last_error",
 )
 
 
@@ -85,6 +86,8 @@ def load(path: str | None = None):
         lib.pp_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]
         lib.pp_profile_read.restype = C.c_int
+        lib.pp_kernel_launches.argtypes = []
+        lib.pp_kernel_launches.restype = C.c_longlong
         lib.pp_destroy.argtypes = [vp]
         lib.pp_destroy.restype = None
         lib.pp_last_error.argtypes = [vp]
@@ -240,6 +243,10 @@ def pp_profile_read(ctx, kernel_id: int):
     fl = C.c_double()
     _check(lib.pp_profile_read(ctx, int(kernel_id), C.byref(n), C.byref(ms), C.byref(fl)), ctx)
     return dict(launches=n.value, ms=ms.value, flops=fl.value)
+
+
+def pp_kernel_launches() -> int:
+    return int(load().pp_kernel_launches())
 
 
 def pp_destroy(ctx):

@@ -7,6 +7,11 @@
 #include <new>
 
 static thread_local std::string g_create_err;
+unsigned long long g_pp_launches = 0;
+
+extern "C" long long pp_kernel_launches(void) {
+  return (long long)__atomic_load_n(&g_pp_launches, __ATOMIC_RELAXED);
+}
 
 extern "C" void pp_default_options(pp_options *opt) {
   if (!opt) return;

@@ -34,8 +34,11 @@ struct PPError {
                     std::string(#call) + " -> " + cudaGetErrorString(e_));                   \
   } while (0)
 
+// every kernel launch of the library is followed by PP_LAUNCH_CHECK, which also counts it
+extern unsigned long long g_pp_launches;
 #define PP_LAUNCH_CHECK(name)                                                                \
   do {                                                                                       \
+    __atomic_fetch_add(&g_pp_launches, 1ull, __ATOMIC_RELAXED);                              \
     cudaError_t e_ = cudaGetLastError();                                                     \
     if (e_ != cudaSuccess) throw PPError(PP_ECUDA, std::string(name) + ": " + cudaGetErrorString(e_)); \
   } while (0)

@@ -291,9 +291,11 @@ void sigma_f64(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met
     SigmaWork<double> wk{c->w_acc.as<double>(), c->w_acc.as<double>() + (long long)R * ov,
                          c->w_tmp.as<double>(), c->w_cq.as<double>(), c->w_W.as<double>(),
                          c->w_U.as<double>(), c->w_EF.as<double>()};
-    auto ladder = [&](int Rc, const double *Cmat, double *P) -> PLayout {
+    SigmaHooks<double> hk;
+    hk.amplitude = [&](int Rc, const double *Cmat, double *Bacc) {
       const long long qov = (long long)Q * ov;
       double *T = c->w_T.as<double>();
+      double *P = c->w_P.as<double>();
       const int si = c->slab_i;
       for (int i0 = 0; i0 < o; i0 += si) {
         const int ni = std::min(si, o - i0);
@@ -306,11 +308,10 @@ void sigma_f64(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met
         p2.C = P + (long long)i0 * v * Q; p2.c_m = Q; p2.c_n = 1; p2.c_batch = qov;
         gemm_f64(p2, c->stream);
       }
-      return PLayout{qov, (long long)Q};
+      apply_cq_of_p<double>(c, Rc, P, qov, (long long)Q, res, Bacc);
     };
     const double *V = Zd + (long long)r0 * ov;
     sigma_chunk<double>(c, R, V, V, sig_d + (long long)r0 * ov,
-                        met_d ? met_d + (long long)r0 * ov : nullptr, res, wk,
-                        c->w_P.as<double>(), ladder);
+                        met_d ? met_d + (long long)r0 * ov : nullptr, res, wk, hk);
   }
 }

@@ -14,6 +14,8 @@
 // ring parts of Eq. (b(2)) into one contraction with the amplitudes; Gam carries
 // the (kc|bi)/(kc|aj) ring parts.  sigma_X = A X + B Y, sigma_Y = B X + A Y.
 #pragma once
+#include <functional>
+
 #include "pp_internal.h"
 
 template <class T> struct SigmaRes {
@@ -22,9 +24,12 @@ template <class T> struct SigmaRes {
 template <class T> struct SigmaWork {
   T *Aacc, *Bacc, *tmp, *cq, *W, *U, *EF;  // sized for R half-vectors
 };
-// P layout chosen by the ladder: element (r, i, c, Q) at r*p_r + (i*v + c)*p_ic + Q
-struct PLayout {
-  long long p_r, p_ic;
+// Backend hooks for the large contractions.  w / ef return false to fall back to the
+// strided SIMT GEMMs; amplitude(R, Cmat, Bacc) must add sum_Q C_Q(T C_Q(V)) into Bacc.
+template <class T> struct SigmaHooks {
+  std::function<bool(int R, const T *V, T *W)> w;                 // W[r][j][Q][d] = (V_r Bvv_Q)[j][d]
+  std::function<bool(int R, const T *V, T *EF, bool second)> ef;  // E (and F) into EF[r][t][i][j]
+  std::function<void(int R, const T *Cmat, T *Bacc)> amplitude;
 };
 
 namespace sigma_detail {
@@ -99,10 +104,9 @@ template <> inline void gemm<float>(const GemmS<float> &g, cudaStream_t s) { gem
 }  // namespace sigma_detail
 
 // One chunk of R half-vectors V (type T, device), outputs in double.
-// ladder(U_as_Cmat, P_out) must fill P with P_Q = T C_Q(V) in the returned layout.
-template <class T, class Ladder>
+template <class T>
 void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *sig, double *met,
-                 const SigmaRes<T> &res, const SigmaWork<T> &wk, T *P, Ladder &&ladder) {
+                 const SigmaRes<T> &res, const SigmaWork<T> &wk, const SigmaHooks<T> &hk) {
   using namespace sigma_detail;
   const int o = c->o, v = c->v, Q = c->Q, order = c->opt.order;
   const long long ov = c->ov;
@@ -131,12 +135,14 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     gemm<T>(j, s);
     T *W = wk.W;  // W[r][j][Q][d] = V_r BvvP
     const long long oQv = (long long)o * Q * v;
-    GemmS<T> w;
-    w.M = o; w.N = Q * v; w.K = v; w.nbatch = R;
-    w.A = V; w.a_m = v; w.a_k = 1; w.a_batch = ov;
-    w.B = res.BvvP; w.b_k = (long long)Q * v; w.b_n = 1;
-    w.C = W; w.c_m = (long long)Q * v; w.c_n = 1; w.c_batch = oQv;
-    gemm<T>(w, s);
+    if (!(hk.w && hk.w(R, V, W))) {
+      GemmS<T> w;
+      w.M = o; w.N = Q * v; w.K = v; w.nbatch = R;
+      w.A = V; w.a_m = v; w.a_k = 1; w.a_batch = ov;
+      w.B = res.BvvP; w.b_k = (long long)Q * v; w.b_n = 1;
+      w.C = W; w.c_m = (long long)Q * v; w.c_n = 1; w.c_batch = oQv;
+      gemm<T>(w, s);
+    }
     GemmS<T> ka;  // KA: Aacc -= sum_Q sum_k Boo[Q][i][k] W[r][k][Q][a]
     ka.M = o; ka.N = v; ka.K = o; ka.nred = Q; ka.nbatch = R;
     ka.A = res.Boo; ka.a_m = o; ka.a_k = 1; ka.a_red = (long long)o * o;
@@ -145,16 +151,18 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     gemm<T>(ka, s);
     T *EF = wk.EF;  // E[r][Q][i][j] = sum_b Bov[Q][i][b] V[r][j][b]; F likewise with Gam
     const long long efb = 2LL * Q * o * o;
-    GemmS<T> e;
-    e.M = Q * o; e.N = o; e.K = v; e.nbatch = R;
-    e.A = res.Bov; e.a_m = v; e.a_k = 1;
-    e.B = V; e.b_k = 1; e.b_n = v; e.b_batch = ov;
-    e.C = EF; e.c_m = o; e.c_n = 1; e.c_batch = efb;
-    gemm<T>(e, s);
-    if (order >= 2) {
-      e.A = res.Gam;
-      e.C = EF + (long long)Q * o * o;
+    if (!(hk.ef && hk.ef(R, V, EF, order >= 2))) {
+      GemmS<T> e;
+      e.M = Q * o; e.N = o; e.K = v; e.nbatch = R;
+      e.A = res.Bov; e.a_m = v; e.a_k = 1;
+      e.B = V; e.b_k = 1; e.b_n = v; e.b_batch = ov;
+      e.C = EF; e.c_m = o; e.c_n = 1; e.c_batch = efb;
       gemm<T>(e, s);
+      if (order >= 2) {
+        e.A = res.Gam;
+        e.C = EF + (long long)Q * o * o;
+        gemm<T>(e, s);
+      }
     }
     GemmS<T> kb;  // Bacc -= sum_t sum_j EF[r][t][i][j] GB[t][j][a]
     kb.M = o; kb.N = v; kb.K = o; kb.nbatch = R;
@@ -180,19 +188,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
       gemm<T>(u, s);
       k_cmat<T><<<ew_grid(R * qov), 256, 0, s>>>(U, W, o, v, Q, R * qov);
       PP_LAUNCH_CHECK("k_cmat");
-      PLayout pl = ladder(R, (const T *)U, P);
-      GemmS<T> f1;  // Bacc += sum_c sum_Q P[r][i][c][Q] Bvv[Q][c][a]
-      f1.M = o; f1.N = v; f1.K = Q; f1.nred = v; f1.nbatch = R;
-      f1.A = P; f1.a_m = v * pl.p_ic; f1.a_k = 1; f1.a_red = pl.p_ic; f1.a_batch = pl.p_r;
-      f1.B = res.Bvv; f1.b_k = (long long)v * v; f1.b_n = 1; f1.b_red = v;
-      f1.C = Bacc; f1.c_m = v; f1.c_n = 1; f1.c_batch = ov; f1.beta = T(1);
-      gemm<T>(f1, s);
-      GemmS<T> f2;  // Bacc -= sum_k sum_Q BooT[i][k][Q] P[r][k][a][Q]
-      f2.M = o; f2.N = v; f2.K = Q; f2.nred = o; f2.nbatch = R;
-      f2.A = res.BooT; f2.a_m = (long long)o * Q; f2.a_k = 1; f2.a_red = Q;
-      f2.B = P; f2.b_k = 1; f2.b_n = pl.p_ic; f2.b_red = v * pl.p_ic; f2.b_batch = pl.p_r;
-      f2.C = Bacc; f2.c_m = v; f2.c_n = 1; f2.c_batch = ov; f2.alpha = T(-1); f2.beta = T(1);
-      gemm<T>(f2, s);
+      hk.amplitude(R, (const T *)U, Bacc);
     }
   }
   if (order >= 2) {
@@ -221,4 +217,26 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     k_metric<T><<<ew_grid(tot), 256, 0, s>>>(met, V64, t1, t3, order >= 2, ov, tot);
     PP_LAUNCH_CHECK("k_metric");
   }
+}
+
+// Bacc += sum_Q C_Q(P_Q) = sum_Q (P_Q Bvv_Q - Boo_Q P_Q) for P with element (r, i, c, Q) at
+// r*p_r + (i*v + c)*p_ic + Q (strided SIMT GEMMs)
+template <class T>
+void apply_cq_of_p(const pp_ctx *c, int R, const T *P, long long p_r, long long p_ic, const SigmaRes<T> &res,
+                   T *Bacc) {
+  using namespace sigma_detail;
+  const int o = c->o, v = c->v, Q = c->Q;
+  const long long ov = c->ov;
+  GemmS<T> f1;  // Bacc += sum_c sum_Q P[r][i][c][Q] Bvv[Q][c][a]
+  f1.M = o; f1.N = v; f1.K = Q; f1.nred = v; f1.nbatch = R;
+  f1.A = P; f1.a_m = v * p_ic; f1.a_k = 1; f1.a_red = p_ic; f1.a_batch = p_r;
+  f1.B = res.Bvv; f1.b_k = (long long)v * v; f1.b_n = 1; f1.b_red = v;
+  f1.C = Bacc; f1.c_m = v; f1.c_n = 1; f1.c_batch = ov; f1.beta = T(1);
+  gemm<T>(f1, c->stream);
+  GemmS<T> f2;  // Bacc -= sum_k sum_Q BooT[i][k][Q] P[r][k][a][Q]
+  f2.M = o; f2.N = v; f2.K = Q; f2.nred = o; f2.nbatch = R;
+  f2.A = res.BooT; f2.a_m = (long long)o * Q; f2.a_k = 1; f2.a_red = Q;
+  f2.B = P; f2.b_k = 1; f2.b_n = p_ic; f2.b_red = v * p_ic; f2.b_batch = p_r;
+  f2.C = Bacc; f2.c_m = v; f2.c_n = 1; f2.c_batch = ov; f2.alpha = T(-1); f2.beta = T(1);
+  gemm<T>(f2, c->stream);
 }

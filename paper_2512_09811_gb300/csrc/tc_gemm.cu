@@ -128,14 +128,30 @@ struct alignas(64) GemmMaps {
   CUtensorMap a[3];
   CUtensorMap b[3];
 };
+// output element (row, col) goes to  (row / d_r) * s_r1 + (row % d_r) * s_r0
+//                                   + (col / d_c) * s_c1 + (col % d_c) * s_c0
+// as FP32 (C, optionally accumulated) or as a BF16 pair (Chi, and Clo = remainder if set)
+struct GemmOut {
+  long long d_r = 1LL << 40, s_r1 = 0, s_r0 = 0, d_c = 1LL << 40, s_c1 = 0, s_c0 = 1;
+  float *C = nullptr;
+  __nv_bfloat16 *Chi = nullptr, *Clo = nullptr;
+  float alpha = 1.f;
+  int accumulate = 0;
+};
 struct GemmArgs {
   int M, N, nk, nseg;
-  float alpha;
-  int accumulate;
-  float *C;
-  long long ldc;
+  GemmOut out, out2;  // out2 is written too when out2.C or out2.Chi is set
   int *err;
 };
+__device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float x) {
+  if (o.C) {
+    o.C[off] = o.accumulate ? x + o.C[off] : x;
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    o.Chi[off] = h;
+    if (o.Clo) o.Clo[off] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ GemmMaps maps, GemmArgs args) {
@@ -202,19 +218,33 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
   if (!ok && lane == 0) atomicExch(args.err, 3);
   tc_fence_after();
   if (ok) {
+    const GemmOut &o = args.out;
+    const GemmOut &o2 = args.out2;
+    const bool two = (o2.C != nullptr) || (o2.Chi != nullptr);
     const int row = m0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const long long rbase = (row / o.d_r) * o.s_r1 + (row % o.d_r) * o.s_r0;
+    const long long rbase2 = two ? (row / o2.d_r) * o2.s_r1 + (row % o2.d_r) * o2.s_r0 : 0;
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + c0, v);
       if (row < args.M) {
-        float *cp = args.C + (long long)row * args.ldc + n0 + c0;
+        const long long col = n0 + c0;
+        long long cb = col / o.d_c, cr = col % o.d_c;
+        long long cb2 = two ? col / o2.d_c : 0, cr2 = two ? col % o2.d_c : 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          if (n0 + c0 + j < args.N) {
-            float x = args.alpha * v[j];
-            if (args.accumulate) x += cp[j];
-            cp[j] = x;
+          if (col + j < args.N) {
+            epi_store(o, rbase + cb * o.s_c1 + cr * o.s_c0, o.alpha * v[j]);
+            if (two) epi_store(o2, rbase2 + cb2 * o2.s_c1 + cr2 * o2.s_c0, o2.alpha * v[j]);
+          }
+          if (++cr == o.d_c) {
+            cr = 0;
+            ++cb;
+          }
+          if (two && ++cr2 == o2.d_c) {
+            cr2 = 0;
+            ++cb2;
           }
         }
       }
@@ -372,6 +402,20 @@ __global__ void k_bovT(const double *__restrict__ Bov, int Q, long long ov, __nv
     if (lo) lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
+// dst[a][c][q] = src[q][c][a] for q < Q (zero for Q <= q < Qp); src [Q][n1][n2] double, dst [n2][n1][Qp]
+__global__ void k_perm_qlast(const double *__restrict__ src, int Q, int n1, int n2, long long Qp,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+  const long long total = (long long)n2 * n1 * Qp;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    long long a = p / ((long long)n1 * Qp), rem = p % ((long long)n1 * Qp);
+    long long c = rem / Qp, q = rem % Qp;
+    float x = (q < Q) ? (float)src[(q * n1 + c) * n2 + a] : 0.f;
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
 __global__ void k_d2f(const double *__restrict__ s, float *__restrict__ d, long long n) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x)
@@ -424,10 +468,10 @@ constexpr int GEMM_BN = 256, GEMM_STAGES = 4, TGEN_STAGES = 3;
 constexpr size_t gemm_smem() { return (size_t)GEMM_STAGES * (BM * BK * 2 + GEMM_BN * BK * 2) + 1024; }
 constexpr size_t tgen_smem() { return (size_t)TGEN_STAGES * 4 * BM * BK * 2 + 1024; }
 
-// C (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K
+// out (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K; output addressing per GemmOut
 void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *A, long long lda,
-               const __nv_bfloat16 *const *B, long long ldb, float *C, long long ldc, float alpha, bool accumulate,
-               int *err, cudaStream_t s) {
+               const __nv_bfloat16 *const *B, long long ldb, const GemmOut &out, int *err, cudaStream_t s,
+               const GemmOut *out2 = nullptr) {
   static bool attr = false;
   if (!attr) {
     PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -440,7 +484,7 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
     maps.a[g] = kmajor_map(A[g], K, M, lda, BM);
     maps.b[g] = kmajor_map(B[g], K, N, ldb, GEMM_BN);
   }
-  GemmArgs a{M, N, (int)(K / BK), nseg, alpha, accumulate ? 1 : 0, C, ldc, err};
+  GemmArgs a{M, N, (int)(K / BK), nseg, out, out2 ? *out2 : GemmOut{}, err};
   dim3 grid((N + GEMM_BN - 1) / GEMM_BN, (M + BM - 1) / BM);
   k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
@@ -479,24 +523,37 @@ struct KernelProfile {
   double ms[2] = {0, 0};
 };
 struct TcPlan {
-  long long ldq = 0, ldT = 0;
+  long long ldq = 0, ldT = 0, vp = 0, Qp = 0;
   KernelProfile prof;
   int slab_i = 1, Rmax = 2;
-  DevBuf bovT_hi, bovT_lo;                     // [ov][ldq]
+  // BF16 hi/lo operands (K-major, K padded to 64)
+  DevBuf bovT_hi, bovT_lo;   // [(i,a)][ldq]       amplitude slab generator
+  DevBuf bvv_hi, bvv_lo;     // [(Q,d)][vp]        W = V Bvv_Q
+  DevBuf bov_hi, bov_lo;     // [(Q,i)][vp]        E = Bov_Q V^T
+  DevBuf gam_hi, gam_lo;     // [(Q,i)][vp]        F = Gam_Q V^T
+  DevBuf bvvT_hi, bvvT_lo;   // [a][(c,Qp)]        sum_Q P_Q Bvv_Q
+  DevBuf booT_hi, booT_lo;   // [i][(k,Qp)]        sum_Q Boo_Q P_Q
+  // FP32 copies of the operands of the remaining SIMT contractions
   DevBuf f_gap, f_eps, f_Bov, f_Boo, f_Bvv, f_BvvP, f_BooT, f_GB, f_Gam, f_poo, f_qoo, f_pvv, f_qvv;
-  DevBuf w_V, w_acc, w_tmp, w_cq, w_W, w_U, w_EF, w_P;
-  DevBuf c_hi, c_lo;                           // C_Q(V) in BF16 [R*Q][ldT]
-  DevBuf t_hi, t_lo;                           // amplitude slab [slab rows][ldT]
+  // workspaces
+  DevBuf w_V, w_acc, w_tmp, w_cq, w_W, w_U, w_EF;
+  DevBuf v_hi, v_lo;         // [(r,j)][vp]
+  DevBuf c_hi, c_lo;         // C_Q(V): [(r,Q)][ldT]
+  DevBuf t_hi, t_lo;         // amplitude slab [rows][ldT]
+  DevBuf p1_hi, p1_lo;       // P as [(r,i)][(c,Qp)]
+  DevBuf p2_hi, p2_lo;       // P as [(r,a)][(k,Qp)]
   DevBuf err;
 };
 
 void tc_destroy(pp_ctx *c) {
   if (!c->tc) return;
   TcPlan *p = c->tc;
-  DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->f_gap, &p->f_eps, &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP,
-                    &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo, &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V,
-                    &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W, &p->w_U, &p->w_EF, &p->w_P, &p->c_hi,
-                    &p->c_lo, &p->t_hi, &p->t_lo, &p->err};
+  DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->bvv_hi, &p->bvv_lo, &p->bov_hi, &p->bov_lo, &p->gam_hi,
+                    &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_gap, &p->f_eps,
+                    &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
+                    &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
+                    &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
+                    &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err};
   for (DevBuf *b : bufs) b->release();
   for (auto &v : p->prof.ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -534,6 +591,20 @@ static void f32_copy(DevBuf &dst, const DevBuf &src, long long n, cudaStream_t s
     PP_LAUNCH_CHECK("k_d2f");
   }
 }
+// rows x ncol double matrix (row stride lds) -> BF16 hi/lo [rows][ld] (zero padded)
+static void bf16_pair(DevBuf &hi, DevBuf &lo, const double *src, long long rows, long long ncol, long long lds,
+                      long long ld, cudaStream_t s) {
+  const size_t n = (size_t)std::max<long long>(rows * ld, 1);
+  hi.ensure(sizeof(__nv_bfloat16) * n);
+  lo.ensure(sizeof(__nv_bfloat16) * n);
+  if (rows * ld > 0) {
+    tc::k_to_bf16<double><<<tc::grid_for(rows * ld), 256, 0, s>>>(src, rows, ncol, lds, hi.as<__nv_bfloat16>(),
+                                                                  lo.as<__nv_bfloat16>(), ld);
+    PP_LAUNCH_CHECK("k_to_bf16");
+  }
+}
+
+static long long pad64(long long x) { return std::max<long long>(tc::BK, ((x + tc::BK - 1) / tc::BK) * tc::BK); }
 
 static TcPlan *tc_plan(pp_ctx *c) {
   if (c->tc) return c->tc;
@@ -541,9 +612,10 @@ static TcPlan *tc_plan(pp_ctx *c) {
   c->tc = p;
   const long long o = c->o, v = c->v, Q = c->Q, ov = c->ov;
   cudaStream_t s = c->stream;
-  p->ldq = std::max<long long>(tc::BK, ((Q + tc::BK - 1) / tc::BK) * tc::BK);
-  p->ldT = ((ov + tc::BK - 1) / tc::BK) * tc::BK;
-  // resident FP32 copies of the small-term operands
+  p->ldq = pad64(Q);
+  p->ldT = pad64(ov);
+  p->vp = pad64(v);
+  p->Qp = pad64(Q);
   f32_copy(p->f_gap, c->gap, ov, s);
   f32_copy(p->f_eps, c->eps, c->n, s);
   f32_copy(p->f_Bov, c->Bov, Q * ov, s);
@@ -557,35 +629,61 @@ static TcPlan *tc_plan(pp_ctx *c) {
   f32_copy(p->f_qoo, c->q_oo, o * o, s);
   f32_copy(p->f_pvv, c->p_vv, v * v, s);
   f32_copy(p->f_qvv, c->q_vv, v * v, s);
-  if (c->opt.order >= 2) {
+  if (c->opt.order >= 1 && Q > 0) {
+    bf16_pair(p->bvv_hi, p->bvv_lo, c->Bvv.as<double>(), Q * v, v, v, p->vp, s);
+    bf16_pair(p->bov_hi, p->bov_lo, c->Bov.as<double>(), Q * o, v, v, p->vp, s);
+    bf16_pair(p->gam_hi, p->gam_lo, c->Gam.as<double>(), Q * o, v, v, p->vp, s);
+  }
+  if (c->opt.order >= 2 && Q > 0) {
     p->bovT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
     p->bovT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
     tc::k_bovT<<<tc::grid_for(ov * p->ldq), 256, 0, s>>>(c->Bov.as<double>(), (int)Q, ov,
                                                          p->bovT_hi.as<__nv_bfloat16>(),
                                                          p->bovT_lo.as<__nv_bfloat16>(), p->ldq);
     PP_LAUNCH_CHECK("k_bovT");
+    p->bvvT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)v * v * p->Qp);
+    p->bvvT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)v * v * p->Qp);
+    tc::k_perm_qlast<<<tc::grid_for(v * v * p->Qp), 256, 0, s>>>(c->Bvv.as<double>(), (int)Q, (int)v, (int)v,
+                                                                 p->Qp, p->bvvT_hi.as<__nv_bfloat16>(),
+                                                                 p->bvvT_lo.as<__nv_bfloat16>());
+    PP_LAUNCH_CHECK("k_perm_qlast");
+    p->booT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)o * o * p->Qp);
+    p->booT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)o * o * p->Qp);
+    tc::k_perm_qlast<<<tc::grid_for(o * o * p->Qp), 256, 0, s>>>(c->Boo.as<double>(), (int)Q, (int)o, (int)o,
+                                                                 p->Qp, p->booT_hi.as<__nv_bfloat16>(),
+                                                                 p->booT_lo.as<__nv_bfloat16>());
+    PP_LAUNCH_CHECK("k_perm_qlast");
   }
-  // workspaces: R half-vectors per chunk; the amplitude slab keeps ~64 MB of BF16
-  const long long per_half = 3 * Q * ov + 2 * Q * o * o + 8 * ov + Q;
-  long long R = (8LL << 30) / (4 * per_half + 4 * Q * p->ldT);
+  // chunk of R half-vectors: FP32 W, U, E/F plus BF16 C_Q(V) and two BF16 copies of P
+  const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 2 * 2 * Q * p->ldT +
+                             2 * 2 * 2 * ov * p->Qp;
+  long long R = (12LL << 30) / std::max<long long>(per_half, 1);
   R = std::max<long long>(2, std::min<long long>(R, 64));
   R &= ~1LL;
   p->Rmax = (int)R;
-  const long long si = std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
-  p->slab_i = (int)si;
+  p->slab_i = (int)std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
   p->err.ensure(sizeof(int) * 4);
   PP_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int) * 4, s));
   return p;
 }
 
-// BF16 tensor-core sigma: small terms in FP32, amplitude contraction on tcgen05.
-// split = true uses hi/lo BF16 pairs (three products) for an FP32-level result.
+static void ensure_zeroed(DevBuf &b, size_t bytes, cudaStream_t s) {
+  if (bytes <= b.bytes) return;
+  b.ensure(bytes);
+  PP_CUDA(cudaMemsetAsync(b.p, 0, b.bytes, s));
+}
+
+// BF16 tensor-core sigma: amplitude contraction and the large first-order contractions on
+// tcgen05; the remaining small contractions in FP32.  split = true uses hi/lo BF16 pairs
+// (three products) for an FP32-level result.
 void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split) {
   TcPlan *p = tc_plan(c);
   const int o = c->o, v = c->v, Q = c->Q;
-  const long long ov = c->ov;
+  const long long ov = c->ov, vp = p->vp, Qp = p->Qp, ldT = p->ldT;
   cudaStream_t s = c->stream;
   const int Rmax = p->Rmax;
+  const int nseg = split ? 3 : 1;
+  using bf = __nv_bfloat16;
   p->w_V.ensure(sizeof(float) * (size_t)Rmax * ov);
   p->w_acc.ensure(sizeof(float) * 2 * (size_t)Rmax * ov);
   p->w_tmp.ensure(sizeof(float) * 4 * (size_t)Rmax * ov);
@@ -593,20 +691,32 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     p->w_cq.ensure(sizeof(float) * (size_t)Q * Rmax);
     p->w_W.ensure(sizeof(float) * (size_t)Rmax * o * Q * v);
     p->w_EF.ensure(sizeof(float) * (size_t)Rmax * 2 * Q * o * o);
+    p->v_hi.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
+    p->v_lo.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
   }
   if (c->opt.order >= 2) {
     p->w_U.ensure(sizeof(float) * (size_t)Rmax * Q * ov);
-    p->w_P.ensure(sizeof(float) * (size_t)Rmax * Q * ov);
-    p->c_hi.ensure(sizeof(__nv_bfloat16) * (size_t)Rmax * Q * p->ldT);
-    if (split) p->c_lo.ensure(sizeof(__nv_bfloat16) * (size_t)Rmax * Q * p->ldT);
-    p->t_hi.ensure(sizeof(__nv_bfloat16) * (size_t)p->slab_i * v * p->ldT);
-    if (split) p->t_lo.ensure(sizeof(__nv_bfloat16) * (size_t)p->slab_i * v * p->ldT);
+    p->c_hi.ensure(sizeof(bf) * (size_t)Rmax * Q * ldT);
+    p->c_lo.ensure(sizeof(bf) * (size_t)Rmax * Q * ldT);
+    p->t_hi.ensure(sizeof(bf) * (size_t)p->slab_i * v * ldT);
+    p->t_lo.ensure(sizeof(bf) * (size_t)p->slab_i * v * ldT);
+    const size_t pbytes = sizeof(bf) * (size_t)Rmax * ov * Qp;  // padding columns stay zero
+    ensure_zeroed(p->p1_hi, pbytes, s);
+    ensure_zeroed(p->p1_lo, pbytes, s);
+    ensure_zeroed(p->p2_hi, pbytes, s);
+    ensure_zeroed(p->p2_lo, pbytes, s);
   }
   SigmaRes<float> res{p->f_gap.as<float>(), p->f_eps.as<float>(), p->f_Bov.as<float>(), p->f_Boo.as<float>(),
                       p->f_Bvv.as<float>(), p->f_BvvP.as<float>(), p->f_BooT.as<float>(), p->f_GB.as<float>(),
                       p->f_Gam.as<float>(), p->f_poo.as<float>(), p->f_qoo.as<float>(), p->f_pvv.as<float>(),
                       p->f_qvv.as<float>()};
   int *err = p->err.as<int>();
+  const bf *vhi = p->v_hi.as<bf>(), *vlo = p->v_lo.as<bf>();
+  auto seg3 = [&](const bf *hiA, const bf *loA, const bf *hiB, const bf *loB, const bf **A, const bf **B) {
+    A[0] = hiA; B[0] = hiB;
+    A[1] = hiA; B[1] = loB;
+    A[2] = loA; B[2] = hiB;
+  };
   const int R_total = 2 * nvec;
   for (int r0 = 0; r0 < R_total; r0 += Rmax) {
     const int R = std::min(Rmax, R_total - r0);
@@ -614,48 +724,122 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     float *V = p->w_V.as<float>();
     tc::k_d2f<<<tc::grid_for((long long)R * ov), 256, 0, s>>>(V64, V, (long long)R * ov);
     PP_LAUNCH_CHECK("k_d2f");
+    if (c->opt.order >= 1) {
+      tc::k_to_bf16<double><<<tc::grid_for((long long)R * o * vp), 256, 0, s>>>(
+          V64, (long long)R * o, v, v, p->v_hi.as<bf>(), p->v_lo.as<bf>(), vp);
+      PP_LAUNCH_CHECK("k_to_bf16");
+    }
     SigmaWork<float> wk{p->w_acc.as<float>(), p->w_acc.as<float>() + (long long)R * ov, p->w_tmp.as<float>(),
                         p->w_cq.as<float>(), p->w_W.as<float>(), p->w_U.as<float>(), p->w_EF.as<float>()};
-    auto ladder = [&](int Rc, const float *Cmat, float *P) -> PLayout {
+    SigmaHooks<float> hk;
+    hk.w = [&](int Rc, const float *, float *W) {
+      // W[(r,j)][(Q,d)] = sum_b V[(r,j)][b] Bvv[(Q,d)][b]
+      const bf *A[3], *B[3];
+      seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
+      tc::GemmOut out;
+      out.C = W;
+      out.s_r0 = (long long)Q * v;
+      tc::gemm_bf16(Rc * o, Q * v, vp, nseg, A, vp, B, vp, out, err, s);
+      return true;
+    };
+    hk.ef = [&](int Rc, const float *, float *EF, bool second) {
+      // EF[r][t][i][j] = sum_b X_t[i][b] V_r[j][b] with X = Bov (t < Q) and Gam (t >= Q)
+      const bf *A[3], *B[3];
+      tc::GemmOut out;
+      out.d_r = o;
+      out.s_r1 = (long long)o * o;
+      out.s_r0 = o;
+      out.d_c = o;
+      out.s_c1 = 2LL * Q * o * o;
+      out.s_c0 = 1;
+      out.C = EF;
+      seg3(p->bov_hi.as<bf>(), p->bov_lo.as<bf>(), vhi, vlo, A, B);
+      tc::gemm_bf16(Q * o, Rc * o, vp, nseg, A, vp, B, vp, out, err, s);
+      if (second) {
+        out.C = EF + (long long)Q * o * o;
+        seg3(p->gam_hi.as<bf>(), p->gam_lo.as<bf>(), vhi, vlo, A, B);
+        tc::gemm_bf16(Q * o, Rc * o, vp, nseg, A, vp, B, vp, out, err, s);
+      }
+      return true;
+    };
+    hk.amplitude = [&](int Rc, const float *Cmat, float *Bacc) {
       const long long NC = (long long)Rc * Q;
-      __nv_bfloat16 *chi = p->c_hi.as<__nv_bfloat16>();
-      __nv_bfloat16 *clo = split ? p->c_lo.as<__nv_bfloat16>() : nullptr;
-      tc::k_to_bf16<float><<<tc::grid_for(NC * p->ldT), 256, 0, s>>>(Cmat, NC, ov, ov, chi, clo, p->ldT);
+      bf *chi = p->c_hi.as<bf>(), *clo = p->c_lo.as<bf>();
+      tc::k_to_bf16<float><<<tc::grid_for(NC * ldT), 256, 0, s>>>(Cmat, NC, ov, ov, chi, clo, ldT);
       PP_LAUNCH_CHECK("k_to_bf16");
-      __nv_bfloat16 *thi = p->t_hi.as<__nv_bfloat16>();
-      __nv_bfloat16 *tlo = split ? p->t_lo.as<__nv_bfloat16>() : nullptr;
+      bf *thi = p->t_hi.as<bf>();
+      bf *tlo = split ? p->t_lo.as<bf>() : nullptr;
+      bf *p1h = p->p1_hi.as<bf>(), *p1l = split ? p->p1_lo.as<bf>() : nullptr;
+      bf *p2h = p->p2_hi.as<bf>(), *p2l = split ? p->p2_lo.as<bf>() : nullptr;
       const int si = p->slab_i;
       for (int i0 = 0; i0 < o; i0 += si) {
         const int ni = std::min(si, o - i0);
         const long long rows = (long long)ni * v;
-        if (p->ldT > ov) {  // zero the K padding of the slab rows
-          PP_CUDA(cudaMemset2DAsync(thi + ov, p->ldT * 2, 0, (p->ldT - ov) * 2, rows, s));
-          if (tlo) PP_CUDA(cudaMemset2DAsync(tlo + ov, p->ldT * 2, 0, (p->ldT - ov) * 2, rows, s));
+        if (ldT > ov) {  // zero the K padding of the slab rows
+          PP_CUDA(cudaMemset2DAsync(thi + ov, ldT * 2, 0, (ldT - ov) * 2, rows, s));
+          if (tlo) PP_CUDA(cudaMemset2DAsync(tlo + ov, ldT * 2, 0, (ldT - ov) * 2, rows, s));
         }
         prof_mark(p->prof, 1, s);
-        tc::tgen(p->bovT_hi.as<__nv_bfloat16>(), split ? p->bovT_lo.as<__nv_bfloat16>() : nullptr, p->ldq, ov, o,
-                 v, i0, ni, c->eps.as<double>(), thi, tlo, p->ldT, err, s);
+        tc::tgen(p->bovT_hi.as<bf>(), split ? p->bovT_lo.as<bf>() : nullptr, p->ldq, ov, o, v, i0, ni,
+                 c->eps.as<double>(), thi, tlo, ldT, err, s);
         prof_mark(p->prof, 1, s);
         if (p->prof.on) {
           p->prof.launches[1] += 1;
-          p->prof.flops[1] += 2.0 * 2.0 * (double)Q * (double)rows * (double)ov * (split ? 3 : 1);
+          p->prof.flops[1] += 2.0 * 2.0 * (double)Q * (double)rows * (double)ov * nseg;
         }
-        // P rows (i,c) of this slab: P[(i,c)][(r,Q)] (row stride NC)
-        const __nv_bfloat16 *A[3] = {thi, thi, tlo};
-        const __nv_bfloat16 *B[3] = {chi, clo, chi};
+        // P = T C^T for this slab, written as BF16 pairs in two layouts:
+        //   P1[r][i][c][q] (rows (r,i), K = (c,q)) and P2[r][c][i][q] (rows (r,c), K = (i,q))
+        const bf *A[3] = {thi, thi, tlo};
+        const bf *B[3] = {chi, clo, chi};
+        tc::GemmOut o1, o2;
+        o1.Chi = p1h + (long long)i0 * v * Qp;
+        o1.Clo = p1l ? p1l + (long long)i0 * v * Qp : nullptr;
+        o1.s_r0 = Qp;
+        o1.d_c = Q;
+        o1.s_c1 = ov * Qp;
+        o2.Chi = p2h + (long long)i0 * Qp;
+        o2.Clo = p2l ? p2l + (long long)i0 * Qp : nullptr;
+        o2.d_r = v;
+        o2.s_r1 = Qp;
+        o2.s_r0 = (long long)o * Qp;
+        o2.d_c = Q;
+        o2.s_c1 = ov * Qp;
         prof_mark(p->prof, 0, s);
-        tc::gemm_bf16((int)rows, (int)NC, p->ldT, split ? 3 : 1, A, p->ldT, B, p->ldT,
-                      P + (long long)i0 * v * NC, NC, 1.0f, false, err, s);
+        tc::gemm_bf16((int)rows, (int)NC, ldT, nseg, A, ldT, B, ldT, o1, err, s, &o2);
         prof_mark(p->prof, 0, s);
         if (p->prof.on) {
           p->prof.launches[0] += 1;
-          p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov * (split ? 3 : 1);
+          p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov * nseg;
         }
       }
-      return PLayout{(long long)Q, NC};
+      // Bacc[(r,i)][a] += sum_(c,q) P1[(r,i)][(c,q)] Bvv[q][c][a]
+      {
+        const bf *A[3], *B[3];
+        seg3(p->p1_hi.as<bf>(), p->p1_lo.as<bf>(), p->bvvT_hi.as<bf>(), p->bvvT_lo.as<bf>(), A, B);
+        tc::GemmOut out;
+        out.C = Bacc;
+        out.s_r0 = v;
+        out.accumulate = 1;
+        tc::gemm_bf16(Rc * o, v, (long long)v * Qp, nseg, A, (long long)v * Qp, B, (long long)v * Qp, out, err, s);
+      }
+      // Bacc[r][i][a] -= sum_(k,q) P2[(r,a)][(k,q)] Boo[q][i][k]   (rows (r,a), columns i)
+      {
+        const bf *A[3], *B[3];
+        seg3(p->p2_hi.as<bf>(), p->p2_lo.as<bf>(), p->booT_hi.as<bf>(), p->booT_lo.as<bf>(), A, B);
+        tc::GemmOut out;
+        out.C = Bacc;
+        out.d_r = v;
+        out.s_r1 = ov;
+        out.s_r0 = 1;
+        out.s_c0 = v;
+        out.alpha = -1.f;
+        out.accumulate = 1;
+        tc::gemm_bf16(Rc * v, o, (long long)o * Qp, nseg, A, (long long)o * Qp, B, (long long)o * Qp, out, err,
+                      s);
+      }
     };
     sigma_chunk<float>(c, R, V, V64, sig_d + (long long)r0 * ov, met_d ? met_d + (long long)r0 * ov : nullptr,
-                       res, wk, p->w_P.as<float>(), ladder);
+                       res, wk, hk);
   }
   int herr = 0;
   PP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
