@@ -6,6 +6,8 @@
 // 16-deep K steps staged in shared memory, 4x4 register blocking per thread.
 #include "pp_internal.h"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
@@ -17,7 +19,20 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmS<T> g) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const long long m0 = (long long)blockIdx.y * TM, n0 = (long long)blockIdx.x * TN;
-  const long long b = blockIdx.z;
+  const long long b = blockIdx.z / g.ksplit;
+  const int ks = blockIdx.z % g.ksplit;
+  // this block's share of the reduction: a range of t (nred > 1) or of K (nred == 1)
+  int t_lo = 0, t_hi = g.nred, k_lo = 0, k_hi = g.K;
+  if (g.ksplit > 1) {
+    if (g.nred > 1) {
+      t_lo = (int)((long long)g.nred * ks / g.ksplit);
+      t_hi = (int)((long long)g.nred * (ks + 1) / g.ksplit);
+    } else {
+      const int nk = (g.K + TK - 1) / TK;
+      k_lo = (int)((long long)nk * ks / g.ksplit) * TK;
+      k_hi = min(g.K, (int)((long long)nk * (ks + 1) / g.ksplit) * TK);
+    }
+  }
   const T *A = g.A + b * g.a_batch;
   const T *B = g.B + b * g.b_batch;
   T acc[4][4];
@@ -27,10 +42,10 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmS<T> g) {
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   const bool a_mfast = (g.a_m == 1);
   const bool b_nfast = (g.b_n == 1);
-  for (int t = 0; t < g.nred; ++t) {
+  for (int t = t_lo; t < t_hi; ++t) {
     const T *At = A + (long long)t * g.a_red;
     const T *Bt = B + (long long)t * g.b_red;
-    for (int k0 = 0; k0 < g.K; k0 += TK) {
+    for (int k0 = k_lo; k0 < k_hi; k0 += TK) {
 #pragma unroll
       for (int e = 0; e < (TK * TM) / NT; ++e) {
         int idx = tid + e * NT;
@@ -44,7 +59,7 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmS<T> g) {
         }
         long long gm = m0 + mm;
         int gk = k0 + kk;
-        As[kk][mm] = (gm < g.M && gk < g.K) ? At[gm * g.a_m + (long long)gk * g.a_k] : T(0);
+        As[kk][mm] = (gm < g.M && gk < k_hi) ? At[gm * g.a_m + (long long)gk * g.a_k] : T(0);
       }
 #pragma unroll
       for (int e = 0; e < (TK * TN) / NT; ++e) {
@@ -59,7 +74,7 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmS<T> g) {
         }
         long long gn = n0 + nn;
         int gk = k0 + kk;
-        Bs[kk][nn] = (gn < g.N && gk < g.K) ? Bt[(long long)gk * g.b_k + gn * g.b_n] : T(0);
+        Bs[kk][nn] = (gn < g.N && gk < k_hi) ? Bt[(long long)gk * g.b_k + gn * g.b_n] : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -87,6 +102,10 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmS<T> g) {
       long long gn = n0 + tx * 4 + j;
       if (gn >= g.N) continue;
       T *cp = C + gm * g.c_m + gn * g.c_n;
+      if (g.ksplit > 1) {
+        atomicAdd(cp, g.alpha * acc[i][j]);
+        continue;
+      }
       T val = g.alpha * acc[i][j];
       if (g.beta != T(0)) val += g.beta * (*cp);
       *cp = val;
@@ -164,7 +183,8 @@ __global__ void __launch_bounds__(NT) k_tslab_f64(const double *__restrict__ Bov
 
 template <class T> static void gemm_launch(const GemmS<T> &g, cudaStream_t s, const char *name) {
   if (g.M <= 0 || g.N <= 0 || g.nbatch <= 0) return;
-  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.nbatch);
+  if (g.ksplit > 1 && g.beta != T(1)) throw PPError(PP_EINVAL, std::string(name) + ": ksplit needs beta = 1");
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.nbatch * std::max(1, g.ksplit));
   if (grid.y > 65535 || grid.z > 65535) throw PPError(PP_EINVAL, std::string(name) + ": grid too large");
   k_gemm<T><<<grid, NT, 0, s>>>(g);
   PP_LAUNCH_CHECK(name);

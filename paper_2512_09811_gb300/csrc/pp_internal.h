@@ -72,6 +72,10 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 template <class T> struct GemmS {
   int M = 0, N = 0, K = 0, nred = 1, nbatch = 1;
+  // ksplit > 1 splits the reduction (over nred, or over K when nred == 1) across blocks and
+  // accumulates alpha * partial into C atomically; it requires beta == 1 (C already holds
+  // the addend, zero it first for a plain product)
+  int ksplit = 1;
   const T *A = nullptr;
   long long a_m = 0, a_k = 0, a_red = 0, a_batch = 0;
   const T *B = nullptr;

@@ -97,6 +97,8 @@ __global__ void k_combine(double *__restrict__ sig, const T *__restrict__ Aacc,
     sig[p] = (double)Aacc[p] + (double)Bacc[(r ^ 1) * ov + e];
   }
 }
+// FP32 sums may be split across blocks (atomic, order-dependent rounding); FP64 stays deterministic
+template <class T> constexpr bool split_k() { return sizeof(T) == 4; }
 template <class T> inline void gemm(const GemmS<T> &g, cudaStream_t s);
 template <> inline void gemm<double>(const GemmS<double> &g, cudaStream_t s) { gemm_f64(g, s); }
 template <> inline void gemm<float>(const GemmS<float> &g, cudaStream_t s) { gemm_f32(g, s); }
@@ -124,6 +126,11 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     g.A = res.Bov; g.a_m = ov; g.a_k = 1;
     g.B = V; g.b_k = 1; g.b_n = ov;
     g.C = cq; g.c_m = R; g.c_n = 1;
+    if (split_k<T>()) {  // few output tiles, long K: split K across blocks
+      PP_CUDA(cudaMemsetAsync(cq, 0, sizeof(T) * (size_t)Q * R, s));
+      g.beta = T(1);
+      g.ksplit = 32;
+    }
     gemm<T>(g, s);
     GemmS<T> j;  // J into both accumulators
     j.M = R; j.N = (int)ov; j.K = Q;
@@ -148,6 +155,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     ka.A = res.Boo; ka.a_m = o; ka.a_k = 1; ka.a_red = (long long)o * o;
     ka.B = W; ka.b_k = (long long)Q * v; ka.b_n = 1; ka.b_red = v; ka.b_batch = oQv;
     ka.C = Aacc; ka.c_m = v; ka.c_n = 1; ka.c_batch = ov; ka.alpha = T(-1); ka.beta = T(1);
+    if (split_k<T>()) ka.ksplit = 16;
     gemm<T>(ka, s);
     T *EF = wk.EF;  // E[r][Q][i][j] = sum_b Bov[Q][i][b] V[r][j][b]; F likewise with Gam
     const long long efb = 2LL * Q * o * o;
@@ -176,6 +184,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
       kb.nred = Q;
       kb.B = res.Bov;
     }
+    if (split_k<T>()) kb.ksplit = 16;
     gemm<T>(kb, s);
     if (order >= 2) {
       T *U = wk.U;  // U[r][Q][l][b] = Boo_Q V_r, then C_Q(V) = W - U in place

@@ -85,6 +85,110 @@ __global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int p, 
   *g = alpha * s + (beta != 0.0 ? beta * (*g) : 0.0);
 }
 
+// ---- 2-D tiled Gram: part[chunk][i][j] = sum_{l in chunk} A_i[l] B_j[l], 32 x 32 pair tiles ---
+constexpr int GT = 32, GRT = 32;
+__global__ void __launch_bounds__(256) k_gram2d(const double *__restrict__ A, long long lda, int p,
+                                                const double *__restrict__ B, long long ldb, int q,
+                                                long long L, long long chunk, int ntq,
+                                                double *__restrict__ part) {
+  __shared__ double As[GT][GRT + 1];
+  __shared__ double Bs[GT][GRT + 1];
+  const int ti = blockIdx.x / ntq, tj = blockIdx.x % ntq;
+  const int i0 = ti * GT, j0 = tj * GT;
+  const long long l0 = blockIdx.y * chunk, l1 = min(L, l0 + chunk);
+  const int tid = threadIdx.x;
+  const int oi = tid >> 3, oj = (tid & 7) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long r0 = l0; r0 < l1; r0 += GRT) {
+    for (int idx = tid; idx < GT * GRT; idx += 256) {
+      int i = idx / GRT, rr = idx % GRT;
+      long long l = r0 + rr;
+      As[i][rr] = (i0 + i < p && l < l1) ? A[(long long)(i0 + i) * lda + l] : 0.0;
+      Bs[i][rr] = (j0 + i < q && l < l1) ? B[(long long)(j0 + i) * ldb + l] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GRT; ++rr) {
+      const double a = As[oi][rr];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] = fma(a, Bs[oj + t][rr], acc[t]);
+    }
+    __syncthreads();
+  }
+  const long long base = (long long)blockIdx.y * p * q;
+  for (int t = 0; t < 4; ++t) {
+    const int i = i0 + oi, j = j0 + oj + t;
+    if (i < p && j < q) part[base + (long long)i * q + j] = acc[t];
+  }
+}
+
+// ---- tall-skinny combine: Y[j][l] = alpha sum_k V[k][l] C[j][k] + beta Y[j][l], j < q ------
+constexpr int CTS = 16;
+__global__ void __launch_bounds__(256) k_combine_ts(const double *__restrict__ V, long long ldv, int m,
+                                                    const double *__restrict__ C, int ldc, int q,
+                                                    double *__restrict__ Y, long long ldy, long long L,
+                                                    double alpha, double beta) {
+  __shared__ double Cs[CTS][MAXM];
+  const int j0 = blockIdx.y * CTS;
+  const int nj = min(CTS, q - j0);
+  for (int idx = threadIdx.x; idx < nj * m; idx += blockDim.x) {
+    int j = idx / m, k = idx % m;
+    Cs[j][k] = C[(long long)(j0 + j) * ldc + k];
+  }
+  __syncthreads();
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double acc[CTS];
+#pragma unroll
+  for (int j = 0; j < CTS; ++j) acc[j] = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double vk = V[(long long)k * ldv + l];
+#pragma unroll
+    for (int j = 0; j < CTS; ++j) acc[j] = fma(vk, Cs[j][k], acc[j]);
+  }
+  for (int j = 0; j < nj; ++j) {
+    double *y = Y + (long long)(j0 + j) * ldy + l;
+    *y = alpha * acc[j] + (beta != 0.0 ? beta * (*y) : 0.0);
+  }
+}
+
+// ---- Cholesky QR of a block: G = N^T N (n x n); T (row j = coefficients of new vector j) with
+// N_new_j = sum_k N_k T[j][k]; columns whose pivot falls below tol * G_jj are dropped (T row 0,
+// kept[j] = 0).  One thread (n <= 64).
+__global__ void k_cholqr(const double *__restrict__ Gin, int n, double tol, double *__restrict__ T,
+                         int *__restrict__ kept) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double Lm[64][64];
+  int keep[64];
+  for (int j = 0; j < n; ++j) {
+    double d = Gin[j * n + j];
+    for (int k = 0; k < j; ++k)
+      if (keep[k]) d -= Lm[j][k] * Lm[j][k];
+    keep[j] = (d > tol * Gin[j * n + j] && d > 0.0) ? 1 : 0;
+    const double ljj = keep[j] ? sqrt(d) : 0.0;
+    Lm[j][j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double g = Gin[i * n + j];
+      for (int k = 0; k < j; ++k)
+        if (keep[k]) g -= Lm[i][k] * Lm[j][k];
+      Lm[i][j] = keep[j] ? g / ljj : 0.0;
+    }
+  }
+  for (int idx = 0; idx < n * n; ++idx) T[idx] = 0.0;
+  // row j of L^-1: L^-1 is lower triangular; compute column by column
+  for (int c = 0; c < n; ++c) {
+    if (!keep[c]) continue;
+    for (int i = 0; i < n; ++i) {
+      if (i < c || !keep[i]) continue;
+      double r = (i == c) ? 1.0 : 0.0;
+      for (int t = c; t < i; ++t)
+        if (keep[t]) r -= Lm[i][t] * T[t * n + c];
+      T[i * n + c] = r / Lm[i][i];
+    }
+  }
+  for (int j = 0; j < n; ++j) kept[j] = keep[j];
+}
+
 // ---- parallel cyclic Jacobi for a symmetric m x m matrix (m <= MAXM) -----------------
 // out: evals ascending in lam[m]; eigenvectors as rows E[j*m + i] (component i of vector j)
 __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ Gin, int m,
@@ -148,7 +252,7 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
     }
     tot = red[0];
     __syncthreads();
-    if (off <= 1e-32 * tot || off == 0.0) break;
+    if (off <= 1e-28 * tot || off == 0.0) break;
     for (int r = 0; r < mp - 1; ++r) {
       if (tid < half) {
         int k = tid;
@@ -497,6 +601,7 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
   double *dL = t1 + m;          // m
   __shared__ double red[256];
   __shared__ double qgq[32 * 32];
+  __shared__ double Zs[32 * 32];
   __shared__ int ok_s;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < b; ++j) {
@@ -530,15 +635,21 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
           qgq[p * 32 + q] = s;
         }
         __syncthreads();
+        // Z[i][p] = sum_q Q_q[i] qgq[q][p]  (so Q qgq Q^T = Z Q)
+        for (int idx = tid; idx < m * j; idx += nt) {
+          int i = idx / j, p = idx % j;
+          double z = 0.0;
+          for (int q = 0; q < j; ++q) z += Qc[q * m + i] * qgq[q * 32 + p];
+          Zs[i * 32 + p] = z;
+        }
+        __syncthreads();
         // G <- (1 - QQ^T) G (1 - QQ^T) + gamma QQ^T
         for (int idx = tid; idx < m * m; idx += nt) {
           int i = idx / m, k = idx % m;
           double g = G[i * ld + k];
           for (int p = 0; p < j; ++p) {
-            double qi = Qc[p * m + i], qk = Qc[p * m + k];
-            g -= GQ[i * b + p] * qk + qi * GQ[k * b + p];
-            g += gamma * qi * qk;
-            for (int q = 0; q < j; ++q) g += qi * qgq[p * 32 + q] * Qc[q * m + k];
+            const double qi = Qc[p * m + i], qk = Qc[p * m + k];
+            g += (Zs[i * 32 + p] - GQ[i * b + p]) * qk - qi * GQ[k * b + p] + gamma * qi * qk;
           }
           G[i * ld + k] = g;
         }
@@ -618,7 +729,7 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
 // modified Gram-Schmidt of ncol coefficient vectors K[t][m] (Euclidean); the first nout
 // independent ones go to Q[t][m]; *nkept receives their count.
 __global__ void __launch_bounds__(128) k_mgs(const double *__restrict__ K, int m, int ncol, int nout,
-                                             double *__restrict__ Qo, int *__restrict__ nkept) {
+                                             double *__restrict__ Qo, int *__restrict__ nkept, double tol) {
   __shared__ double red[128];
   __shared__ double v[MAXM];
   int kept = 0;
@@ -639,7 +750,7 @@ __global__ void __launch_bounds__(128) k_mgs(const double *__restrict__ K, int m
     double n1 = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) n1 += v[i] * v[i];
     n1 = blk_sum(n1, red);
-    if (n1 > 1e-20 * n0 && n1 > 0.0) {
+    if (n1 > tol * n0 && n1 > 0.0) {
       double inv = 1.0 / sqrt(n1);
       for (int i = threadIdx.x; i < m; i += blockDim.x) Qo[(long long)kept * m + i] = v[i] * inv;
       ++kept;
@@ -661,20 +772,27 @@ struct Solver {
 
   void gram(const double *A, long long lda, int p, const double *B, long long ldb, int q,
             double *G, int ldg, double alpha = 1.0, double beta = 0.0) {
-    long long nblk = std::min<long long>(std::max<long long>(1, L / 1024), 296);
-    long long chunk = (L + nblk - 1) / nblk;
-    chunk = ((chunk + GR_ROWS - 1) / GR_ROWS) * GR_ROWS;
-    nblk = (L + chunk - 1) / chunk;
-    size_t need = (size_t)nblk * p * q;
+    const int ntp = (p + GT - 1) / GT, ntq = (q + GT - 1) / GT;
+    long long nch = std::max<long long>(1, std::min<long long>(L / 512, 304 / std::max(1, ntp * ntq) + 1));
+    long long chunk = (L + nch - 1) / nch;
+    chunk = ((chunk + GRT - 1) / GRT) * GRT;
+    nch = (L + chunk - 1) / chunk;
+    size_t need = (size_t)nch * p * q;
     if (need > part_elems) throw PPError(PP_ECUDA, "gram scratch too small");
-    k_gram<<<(unsigned)nblk, 256, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, part);
-    PP_LAUNCH_CHECK("k_gram");
-    k_gram_reduce<<<(p * q + 255) / 256, 256, 0, s>>>(part, (int)nblk, p, q, G, ldg, alpha, beta);
+    k_gram2d<<<dim3(ntp * ntq, (unsigned)nch), 256, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, ntq, part);
+    PP_LAUNCH_CHECK("k_gram2d");
+    k_gram_reduce<<<(p * q + 255) / 256, 256, 0, s>>>(part, (int)nch, p, q, G, ldg, alpha, beta);
     PP_LAUNCH_CHECK("k_gram_reduce");
   }
   // Y[:, 0..q) (+)= V[:, 0..m) C with C[j*ldc + i] (column j of C), columns of length L
   void combine(const double *V, int m, const double *C, int ldc, int q, double *Y, double alpha,
                double beta) {
+    if (m <= MAXM) {
+      dim3 grid((unsigned)((L + 255) / 256), (unsigned)((q + CTS - 1) / CTS));
+      k_combine_ts<<<grid, 256, 0, s>>>(V, L, m, C, ldc, q, Y, L, L, alpha, beta);
+      PP_LAUNCH_CHECK("k_combine_ts");
+      return;
+    }
     GemmF64 g;
     g.M = (int)L; g.N = q; g.K = m;
     g.A = V; g.a_m = 1; g.a_k = L;
@@ -693,13 +811,17 @@ struct Window {
   int m = 0;
   double *V = nullptr, *MV = nullptr, *SV = nullptr;  // [m_max][L]
   double *X = nullptr, *MX = nullptr, *SX = nullptr;  // [64][L]
+  double *Vr = nullptr, *MVr = nullptr, *SVr = nullptr;  // [32][L] reduced blocks for the folded step
   double *Hm, *Hs, *Gmm, *Gms, *Gss, *Lm, *Yw, *Cw, *mu, *W, *Ew, *Esel, *thsel, *Cref, *thref, *Kc, *Qk;
+  double *Qr, *hm, *hs, *C0, *Cred;
   int *dstat, *dkept;
   std::vector<double> h_theta, h_res, h_xsx;
   std::vector<int> order;   // Ritz columns sorted by distance of theta to the shift
   std::vector<int> active;  // columns that get a direction this iteration
   bool done = false;
   int adjust = 0;
+  double best_worst = 1e300;  // BF16 phase: best worst-residual seen, and iterations without gain
+  int stall = 0;
 };
 
 }  // namespace
@@ -754,7 +876,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
   // device memory: per window basis (3 m_max vectors), Ritz block (3 x 64), small matrices
   const size_t vecbytes = sizeof(double) * (size_t)L;
   const size_t mm = (size_t)MAXM * MAXM;
-  const size_t per_win = vecbytes * (3 * (size_t)m_max + 3 * 64) + sizeof(double) * 20 * mm + 64;
+  const size_t per_win = vecbytes * (3 * (size_t)m_max + 3 * 64 + 3 * 32) + sizeof(double) * 26 * mm + 64;
   c->s_V.ensure(per_win * nwin);
   c->s_D.ensure(vecbytes * 32 * nwin);
   c->s_MD.ensure(vecbytes * 32 * nwin);
@@ -781,8 +903,12 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       wi.X = take(vecbytes * 64);
       wi.MX = take(vecbytes * 64);
       wi.SX = take(vecbytes * 64);
+      wi.Vr = take(vecbytes * 32);
+      wi.MVr = take(vecbytes * 32);
+      wi.SVr = take(vecbytes * 32);
       double **mats[] = {&wi.Hm, &wi.Hs, &wi.Gmm, &wi.Gms, &wi.Gss, &wi.Lm, &wi.Yw, &wi.Cw, &wi.mu,
-                         &wi.W, &wi.Ew, &wi.Esel, &wi.thsel, &wi.Cref, &wi.thref, &wi.Kc, &wi.Qk};
+                         &wi.W, &wi.Ew, &wi.Esel, &wi.thsel, &wi.Cref, &wi.thref, &wi.Kc, &wi.Qk,
+                         &wi.Qr, &wi.hm, &wi.hs, &wi.C0, &wi.Cred};
       for (double **q : mats) *q = take(sizeof(double) * mm);
       wi.dstat = (int *)take(sizeof(double) * mm);
       wi.dkept = wi.dstat + 4;
@@ -848,7 +974,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
 
   const int max_iter = std::max(1, c->opt.max_iter);
   const double tol_final = c->opt.res_tol;
-  double tol = refine ? std::max(tol_final, 1e-4) : tol_final;
+  double tol = refine ? std::max(tol_final, 1e-5) : tol_final;
   const char *log_env = std::getenv("PP_LOG");
   const bool log_on = log_env && log_env[0] && log_env[0] != '0';
   pp_status fail = PP_OK;
@@ -861,27 +987,53 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       if (wi.done) continue;
       const int m = wi.m;
       const int b = std::min(wi.b, m);
-      // projected pencil and folded Gram matrices
+      // Rayleigh-Ritz on the projected pencil (full basis)
       sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
       sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
-      sv.gram(wi.MV, L, m, wi.MV, L, m, wi.Gmm, m);
-      sv.gram(wi.MV, L, m, wi.SV, L, m, wi.Gms, m);
-      sv.gram(wi.SV, L, m, wi.SV, L, m, wi.Gss, m);
       PP_CUDA(cudaMemsetAsync(wi.dstat, 0, sizeof(int) * 4, s));
       k_chol_rr<<<1, 256, (m * (m + 1) + m) * sizeof(double), s>>>(wi.Hm, wi.Hs, m, wi.Lm, wi.Yw, wi.Cw, wi.dstat);
       PP_LAUNCH_CHECK("k_chol_rr");
       int mp = (m + 1) & ~1;
-      k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 40);
+      k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
       PP_LAUNCH_CHECK("k_jacobi_eig");
       const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
       k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);
       PP_LAUNCH_CHECK("k_rr_select");
-      k_refined<<<1, 256, (m * (m + 1) + 2 * b * m + 3 * m) * sizeof(double), s>>>(
-          wi.Hm, wi.Hs, wi.Gmm, wi.Gms, wi.Gss, m, b, 4, wi.thsel, wi.Esel, wi.Cref, wi.thref, wi.dstat);
+      // folded step in the span of the nr Rayleigh-Ritz vectors nearest the shift: orthonormal
+      // coefficients Qr, reduced blocks V Qr^T, M V Qr^T, Sigma V Qr^T, and their small Grams
+      const int nr = std::min(nsel, 32);
+      k_mgs<<<1, 128, 0, s>>>(wi.Esel, m, nsel, nr, wi.Qr, wi.dkept, 0.0);
+      PP_LAUNCH_CHECK("k_mgs");
+      sv.combine(wi.V, m, wi.Qr, m, nr, wi.Vr, 1.0, 0.0);
+      sv.combine(wi.MV, m, wi.Qr, m, nr, wi.MVr, 1.0, 0.0);
+      sv.combine(wi.SV, m, wi.Qr, m, nr, wi.SVr, 1.0, 0.0);
+      sv.gram(wi.Vr, L, nr, wi.MVr, L, nr, wi.hm, nr);
+      sv.gram(wi.Vr, L, nr, wi.SVr, L, nr, wi.hs, nr);
+      sv.gram(wi.MVr, L, nr, wi.MVr, L, nr, wi.Gmm, nr);
+      sv.gram(wi.MVr, L, nr, wi.SVr, L, nr, wi.Gms, nr);
+      sv.gram(wi.SVr, L, nr, wi.SVr, L, nr, wi.Gss, nr);
+      {  // initial guesses in reduced coordinates: C0[j][p] = Esel_j . Qr_p
+        GemmF64 g;
+        g.M = b; g.N = nr; g.K = m;
+        g.A = wi.Esel; g.a_m = m; g.a_k = 1;
+        g.B = wi.Qr; g.b_k = 1; g.b_n = m;
+        g.C = wi.C0; g.c_m = nr; g.c_n = 1;
+        gemm_f64(g, s);
+      }
+      k_refined<<<1, 256, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
+          wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
       PP_LAUNCH_CHECK("k_refined");
-      sv.combine(wi.V, m, wi.Cref, m, b, wi.X, 1.0, 0.0);
-      sv.combine(wi.MV, m, wi.Cref, m, b, wi.MX, 1.0, 0.0);
-      sv.combine(wi.SV, m, wi.Cref, m, b, wi.SX, 1.0, 0.0);
+      sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);
+      sv.combine(wi.MVr, nr, wi.Cred, nr, b, wi.MX, 1.0, 0.0);
+      sv.combine(wi.SVr, nr, wi.Cred, nr, b, wi.SX, 1.0, 0.0);
+      {  // coefficients of the folded vectors in the full basis (thick restart): Cref = Cred Qr
+        GemmF64 g;
+        g.M = b; g.N = m; g.K = nr;
+        g.A = wi.Cred; g.a_m = nr; g.a_k = 1;
+        g.B = wi.Qr; g.b_k = m; g.b_n = 1;
+        g.C = wi.Cref; g.c_m = m; g.c_n = 1;
+        gemm_f64(g, s);
+      }
       double *dots = scratch;  // [b][3]
       double *theta_d = scratch + 3 * 64;
       double *rn = scratch + 4 * 64;
@@ -921,11 +1073,23 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       std::stable_sort(wi.order.begin(), wi.order.end(), [&](int a, int b2) {
         return fabs(wi.h_theta[a] - wi.shift) < fabs(wi.h_theta[b2] - wi.shift);
       });
-      bool conv = true;
+      // the roots this window needs: the k lowest targets inside [omega0, omega0 + delta]
+      // (select 0) or the k targets nearest omega0 (select 1); only they must meet the tolerance
+      std::vector<int> need;
+      if (c->opt.select == 1) {
+        for (int t = 0; t < b && (int)need.size() < wi.k; ++t) need.push_back(wi.order[t]);
+      } else {
+        std::vector<int> in;
+        for (int j = 0; j < b; ++j)
+          if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
+        std::sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
+        for (int j = 0; j < (int)in.size() && (int)need.size() < wi.k; ++j) need.push_back(in[j]);
+      }
+      bool conv = !need.empty();
       double worst = 0.0;
-      for (int t = 0; t < wi.nev; ++t) {
-        if (!(wi.h_res[wi.order[t]] <= tol)) conv = false;
-        worst = std::max(worst, wi.h_res[wi.order[t]]);
+      for (int j : need) {
+        if (!(wi.h_res[j] <= tol)) conv = false;
+        worst = std::max(worst, wi.h_res[j]);
       }
       if (log_on) {
         std::fprintf(stderr, "[pp] it %d win %d m %d b %d nev %d shift %.6f stat %d,%d worst %.2e |", it, w,
@@ -934,28 +1098,38 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
           std::fprintf(stderr, " %.6f(%.1e)", wi.h_theta[wi.order[t]], wi.h_res[wi.order[t]]);
         std::fprintf(stderr, "\n");
       }
+      if (!conv && refine && cur_prec == PP_BF16) {
+        // the BF16 phase ends when its residuals stop improving: the rest is left to the split form
+        if (worst < 0.7 * wi.best_worst) {
+          wi.best_worst = worst;
+          wi.stall = 0;
+        } else if (++wi.stall >= 8) {
+          int below = 0;
+          for (int j : need)
+            if (wi.h_res[j] <= 1e-3) ++below;
+          if (!need.empty() && 2 * below >= (int)need.size()) conv = true;
+        }
+      }
       if (conv) {
-        double R = 0.0;
-        for (int t = 0; t < wi.nev; ++t) R = std::max(R, fabs(wi.h_theta[wi.order[t]] - wi.shift));
         bool ok = true;
         if (c->opt.select == 0) {
-          int cnt = 0;
-          for (int t = 0; t < wi.nev; ++t) {
-            double th = wi.h_theta[wi.order[t]];
-            if (th >= wi.omega0 && th <= wi.omega0 + wi.delta) ++cnt;
+          double tmin = 1e300, tmax = -1e300;
+          for (int j = 0; j < b; ++j) {
+            tmin = std::min(tmin, wi.h_theta[j]);
+            tmax = std::max(tmax, wi.h_theta[j]);
           }
-          bool low_covered = (wi.shift - R <= wi.omega0);
-          bool top_covered = (wi.shift + R >= wi.omega0 + wi.delta);
+          const bool low_covered = tmin <= wi.omega0;
+          const bool top_ok = ((int)need.size() >= wi.k) || (tmax >= wi.omega0 + wi.delta);
           if (!low_covered) {
-            ok = false;
-            wi.shift = std::max(wi.omega0, wi.shift - 0.5 * R);
-          } else if (cnt < wi.k && !top_covered) {
-            ok = false;
-            if (wi.nev < bcap - 2) {
+            ok = false;  // targets do not reach down to omega0: move the centre down
+            wi.shift = std::max(wi.omega0, wi.shift - 0.5 * (tmin - wi.omega0) - 0.25 * (tmax - tmin));
+          } else if (!top_ok) {
+            ok = false;  // fewer than k in the window and the window is not covered: widen
+            if (wi.b < bcap) {
               wi.nev = std::min(wi.nev + std::max(2, wi.k / 2), bcap - 2);
               wi.b = std::min(bcap, std::max(wi.b, wi.nev + 2));
             } else {
-              wi.shift = wi.shift + 0.5 * R;
+              wi.shift += 0.5 * (tmax - wi.shift);
             }
           }
           if (!ok && ++wi.adjust > 8) ok = true;  // report what has been found
@@ -998,7 +1172,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
                                 cudaMemcpyDeviceToDevice, s));
         const int nout = std::min(64, std::min(m, 2 * b));
-        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept);
+        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
         PP_LAUNCH_CHECK("k_mgs");
         int kept = 0;
         PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1009,6 +1183,8 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         wi.m = kept;
         wi.done = false;
         wi.adjust = 0;
+        wi.stall = 0;
+        wi.best_worst = 1e300;
       }
       continue;
     }
@@ -1029,7 +1205,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
         PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
                                 cudaMemcpyDeviceToDevice, s));
-        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept);
+        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept, 1e-20);
         PP_LAUNCH_CHECK("k_mgs");
         int kept = 0;
         PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1048,32 +1224,48 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         PP_CUDA(cudaMemcpyAsync(wi.SV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
         wi.m = kept;
       }
-      for (int t = 0; t < nd; ++t) {
-        const long long col = pos + t;
-        double *dst_v = wi.V + (long long)wi.m * L;
-        double *dst_mv = wi.MV + (long long)wi.m * L;
-        double *dst_sv = wi.SV + (long long)wi.m * L;
-        PP_CUDA(cudaMemcpyAsync(dst_v, c->s_D.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
-        PP_CUDA(cudaMemcpyAsync(dst_mv, c->s_MD.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
-        PP_CUDA(cudaMemcpyAsync(dst_sv, c->s_SD.as<double>() + col * L, vecbytes, cudaMemcpyDeviceToDevice, s));
-        double *h = scratch + 512;
-        double *nrm = scratch + 512 + 2 * MAXM;
-        sv.gram(dst_v, L, 1, dst_v, L, 1, nrm + 1, 1);
-        for (int pass = 0; pass < 2; ++pass) {
-          sv.gram(wi.V, L, wi.m, dst_v, L, 1, h, 1);
-          sv.combine(wi.V, wi.m, h, wi.m, 1, dst_v, -1.0, 1.0);
-          sv.combine(wi.MV, wi.m, h, wi.m, 1, dst_mv, -1.0, 1.0);
-          sv.combine(wi.SV, wi.m, h, wi.m, 1, dst_sv, -1.0, 1.0);
+      // append the nd new directions, then block CGS2 against V and Cholesky QR (twice) inside
+      // the block; M V and Sigma V follow by the same combinations
+      const int m0 = wi.m;
+      double *Nv = wi.V + (long long)m0 * L, *Nm = wi.MV + (long long)m0 * L, *Ns = wi.SV + (long long)m0 * L;
+      PP_CUDA(cudaMemcpyAsync(Nv, c->s_D.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(Nm, c->s_MD.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(Ns, c->s_SD.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
+      double *H = wi.Kc;      // [nd][m0]
+      double *GN = wi.Qk;     // [nd][nd]
+      double *Tq = wi.Yw;     // [nd][nd]
+      int *kflag = (int *)(scratch + 6144);
+      for (int pass = 0; pass < 2; ++pass) {
+        if (m0 > 0) {
+          sv.gram(Nv, L, nd, wi.V, L, m0, H, m0);  // H[j][k] = N_j . V_k
+          sv.combine(wi.V, m0, H, m0, nd, Nv, -1.0, 1.0);
+          sv.combine(wi.MV, m0, H, m0, nd, Nm, -1.0, 1.0);
+          sv.combine(wi.SV, m0, H, m0, nd, Ns, -1.0, 1.0);
         }
-        sv.gram(dst_v, L, 1, dst_v, L, 1, nrm, 1);
-        double hn[2];
-        PP_CUDA(cudaMemcpyAsync(hn, nrm, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-        PP_CUDA(cudaStreamSynchronize(s));
-        if (!(hn[0] > 1e-14 * hn[1]) || !(hn[0] > 0.0)) continue;  // dependent: drop
-        k_scale3<<<64, 256, 0, s>>>(dst_v, dst_mv, dst_sv, L, nrm);
-        PP_LAUNCH_CHECK("k_scale3");
-        wi.m += 1;
       }
+      int nkeep = nd;
+      for (int qr = 0; qr < 2 && nkeep > 0; ++qr) {
+        sv.gram(Nv, L, nkeep, Nv, L, nkeep, GN, nkeep);
+        k_cholqr<<<1, 32, 0, s>>>(GN, nkeep, qr == 0 ? 1e-14 : 1e-10, Tq, kflag);
+        PP_LAUNCH_CHECK("k_cholqr");
+        std::vector<int> hk(nkeep);
+        PP_CUDA(cudaMemcpyAsync(hk.data(), kflag, sizeof(int) * nkeep, cudaMemcpyDeviceToHost, s));
+        PP_CUDA(cudaStreamSynchronize(s));
+        // new vectors into the X area (free until the next extraction), kept ones compacted back
+        sv.combine(Nv, nkeep, Tq, nkeep, nkeep, wi.X, 1.0, 0.0);
+        sv.combine(Nm, nkeep, Tq, nkeep, nkeep, wi.MX, 1.0, 0.0);
+        sv.combine(Ns, nkeep, Tq, nkeep, nkeep, wi.SX, 1.0, 0.0);
+        int w2 = 0;
+        for (int j = 0; j < nkeep; ++j) {
+          if (!hk[j]) continue;
+          PP_CUDA(cudaMemcpyAsync(Nv + (long long)w2 * L, wi.X + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+          PP_CUDA(cudaMemcpyAsync(Nm + (long long)w2 * L, wi.MX + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+          PP_CUDA(cudaMemcpyAsync(Ns + (long long)w2 * L, wi.SX + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+          ++w2;
+        }
+        nkeep = w2;
+      }
+      wi.m = m0 + nkeep;
       pos += nd;
     }
     c->st_iters = it + 1;
@@ -1087,10 +1279,10 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
   for (int w = 0; w < nwin; ++w) {
     Window &wi = W[w];
     if (!wi.done) st = PP_ENOTCONV;
-    const int nev = std::min<int>(wi.nev, (int)wi.order.size());
+    const int nb = (int)wi.order.size();
     std::vector<int> sel;
     if (c->opt.select == 1) {
-      std::vector<int> cand(wi.order.begin(), wi.order.begin() + nev);
+      std::vector<int> cand(wi.order.begin(), wi.order.end());
       std::stable_sort(cand.begin(), cand.end(), [&](int a, int b2) {
         double da = fabs(wi.h_theta[a] - wi.omega0), db = fabs(wi.h_theta[b2] - wi.omega0);
         return da < db || (da == db && wi.h_theta[a] < wi.h_theta[b2]);
@@ -1098,7 +1290,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       for (int j = 0; j < (int)cand.size() && (int)sel.size() < wi.k; ++j) sel.push_back(cand[j]);
     } else {
       std::vector<int> in;
-      for (int t = 0; t < nev; ++t) {
+      for (int t = 0; t < nb; ++t) {
         int j = wi.order[t];
         if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
       }

@@ -162,7 +162,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // blockIdx.x walks the M tiles: the CTAs resident at one time cover all M tiles of a few N
+  // tiles, so each B tile is fetched from DRAM once and the A operand stays in L2
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -485,7 +487,8 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
     maps.b[g] = kmajor_map(B[g], K, N, ldb, GEMM_BN);
   }
   GemmArgs a{M, N, (int)(K / BK), nseg, out, out2 ? *out2 : GemmOut{}, err};
-  dim3 grid((N + GEMM_BN - 1) / GEMM_BN, (M + BM - 1) / BM);
+  dim3 grid((M + BM - 1) / BM, (N + GEMM_BN - 1) / GEMM_BN);
+  if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
   k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
 }
