@@ -73,7 +73,8 @@ typedef enum {
 } pp_precision;
 
 typedef struct {
-  int prec;            /* pp_precision */
+  int prec;            /* pp_precision of the solver's sigma: PP_FP64, PP_BF16 (with refine)
+                          or PP_BF16X3 throughout */
   int order;           /* 0, 1 or 2 */
   int block;           /* trial vectors per window per iteration (default 8) */
   int m_max;           /* subspace size before a thick restart (default 96, <= 112) */

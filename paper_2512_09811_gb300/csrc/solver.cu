@@ -818,6 +818,8 @@ struct Window {
   std::vector<double> h_theta, h_res, h_xsx;
   std::vector<int> order;   // Ritz columns sorted by distance of theta to the shift
   std::vector<int> active;  // columns that get a direction this iteration
+  int nnew = 0;             // orthonormal new basis vectors staged for this iteration's sigma
+  int bx = 0;               // block size of the last extraction (rows of Cref, columns of X)
   bool done = false;
   int adjust = 0;
   double best_worst = 1e300;  // BF16 phase: best worst-residual seen, and iterations without gain
@@ -987,6 +989,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       if (wi.done) continue;
       const int m = wi.m;
       const int b = std::min(wi.b, m);
+      wi.bx = b;
       // Rayleigh-Ritz on the projected pencil (full basis)
       sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
       sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
@@ -1166,7 +1169,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       all_done = false;
       for (int w = 0; w < nwin; ++w) {
         Window &wi = W[w];
-        const int m = wi.m, b = std::min(wi.b, m);
+        const int m = wi.m, b = wi.bx;
         const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
         PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
         PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
@@ -1190,13 +1193,20 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
     }
     if (all_done) break;
     if (off == 0) continue;
-    run_sigma(off, c->s_D.as<double>(), c->s_MD.as<double>(), c->s_SD.as<double>());
-    int pos = 0;
+    // Each window: thick restart when the basis would overflow, then block CGS2 of its new
+    // directions against the basis and Cholesky QR (twice) among them -- on the vectors
+    // alone.  Products are formed afterwards, of the orthonormal survivors: the part of a
+    // direction left after orthogonalisation can be orders of magnitude smaller than the
+    // direction, and differencing reduced-precision products would amplify their rounding
+    // by that ratio.  The survivors of all windows are packed at the front of s_D for one
+    // batched sigma.
+    int pos = 0, gpos = 0;
     for (int w = 0; w < nwin; ++w) {
       Window &wi = W[w];
+      wi.nnew = 0;
       if (wi.done || wi.active.empty()) continue;
       const int nd = (int)wi.active.size();
-      const int b = std::min(wi.b, wi.m);
+      const int b = wi.bx;
       if (wi.m + nd > m_max) {
         // thick restart: keep the folded vectors and the next Rayleigh-Ritz vectors
         const int keep = std::min(wi.m, std::max(2 * b, m_max - nd - b));
@@ -1210,11 +1220,7 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         int kept = 0;
         PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
         PP_CUDA(cudaStreamSynchronize(s));
-        // X/MX/SX hold the Ritz block that the directions were made from; stage the new
-        // basis in the direction tail (unused now) -- use X buffers after the append instead
-        double *tV = c->s_part.as<double>();
-        (void)tV;
-        double *stage = wi.X + (long long)b * L;  // room for 64 - b vectors
+        double *stage = wi.X + (long long)b * L;  // X is free after the directions: room for 64 - b
         if (kept > 64 - b) kept = 64 - b;
         sv.combine(wi.V, m, wi.Qk, m, kept, stage, 1.0, 0.0);
         PP_CUDA(cudaMemcpyAsync(wi.V, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
@@ -1224,24 +1230,15 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         PP_CUDA(cudaMemcpyAsync(wi.SV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
         wi.m = kept;
       }
-      // append the nd new directions, then block CGS2 against V and Cholesky QR (twice) inside
-      // the block; M V and Sigma V follow by the same combinations
       const int m0 = wi.m;
-      double *Nv = wi.V + (long long)m0 * L, *Nm = wi.MV + (long long)m0 * L, *Ns = wi.SV + (long long)m0 * L;
-      PP_CUDA(cudaMemcpyAsync(Nv, c->s_D.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(Nm, c->s_MD.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(Ns, c->s_SD.as<double>() + (long long)pos * L, vecbytes * nd, cudaMemcpyDeviceToDevice, s));
-      double *H = wi.Kc;      // [nd][m0]
-      double *GN = wi.Qk;     // [nd][nd]
-      double *Tq = wi.Yw;     // [nd][nd]
+      double *Nv = c->s_D.as<double>() + (long long)pos * L;
+      double *H = wi.Kc;   // [nd][m0]
+      double *GN = wi.Qk;  // [nd][nd]
+      double *Tq = wi.Yw;  // [nd][nd]
       int *kflag = (int *)(scratch + 6144);
-      for (int pass = 0; pass < 2; ++pass) {
-        if (m0 > 0) {
-          sv.gram(Nv, L, nd, wi.V, L, m0, H, m0);  // H[j][k] = N_j . V_k
-          sv.combine(wi.V, m0, H, m0, nd, Nv, -1.0, 1.0);
-          sv.combine(wi.MV, m0, H, m0, nd, Nm, -1.0, 1.0);
-          sv.combine(wi.SV, m0, H, m0, nd, Ns, -1.0, 1.0);
-        }
+      for (int pass = 0; pass < 2 && m0 > 0; ++pass) {
+        sv.gram(Nv, L, nd, wi.V, L, m0, H, m0);  // H[j][k] = N_j . V_k
+        sv.combine(wi.V, m0, H, m0, nd, Nv, -1.0, 1.0);
       }
       int nkeep = nd;
       for (int qr = 0; qr < 2 && nkeep > 0; ++qr) {
@@ -1251,22 +1248,33 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
         std::vector<int> hk(nkeep);
         PP_CUDA(cudaMemcpyAsync(hk.data(), kflag, sizeof(int) * nkeep, cudaMemcpyDeviceToHost, s));
         PP_CUDA(cudaStreamSynchronize(s));
-        // new vectors into the X area (free until the next extraction), kept ones compacted back
+        // orthonormalised block staged in X, the kept columns compacted back into place
         sv.combine(Nv, nkeep, Tq, nkeep, nkeep, wi.X, 1.0, 0.0);
-        sv.combine(Nm, nkeep, Tq, nkeep, nkeep, wi.MX, 1.0, 0.0);
-        sv.combine(Ns, nkeep, Tq, nkeep, nkeep, wi.SX, 1.0, 0.0);
+        double *dst = (qr == 1) ? c->s_D.as<double>() + (long long)gpos * L : Nv;
         int w2 = 0;
         for (int j = 0; j < nkeep; ++j) {
           if (!hk[j]) continue;
-          PP_CUDA(cudaMemcpyAsync(Nv + (long long)w2 * L, wi.X + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
-          PP_CUDA(cudaMemcpyAsync(Nm + (long long)w2 * L, wi.MX + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
-          PP_CUDA(cudaMemcpyAsync(Ns + (long long)w2 * L, wi.SX + (long long)j * L, vecbytes, cudaMemcpyDeviceToDevice, s));
+          PP_CUDA(cudaMemcpyAsync(dst + (long long)w2 * L, wi.X + (long long)j * L, vecbytes,
+                                  cudaMemcpyDeviceToDevice, s));
           ++w2;
         }
         nkeep = w2;
       }
-      wi.m = m0 + nkeep;
+      wi.nnew = nkeep;
+      gpos += nkeep;
       pos += nd;
+    }
+    if (gpos > 0) run_sigma(gpos, c->s_D.as<double>(), c->s_MD.as<double>(), c->s_SD.as<double>());
+    gpos = 0;
+    for (int w = 0; w < nwin; ++w) {
+      Window &wi = W[w];
+      if (wi.nnew == 0) continue;
+      const long long at = (long long)wi.m * L, from = (long long)gpos * L;
+      PP_CUDA(cudaMemcpyAsync(wi.V + at, c->s_D.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.MV + at, c->s_MD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.SV + at, c->s_SD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      wi.m += wi.nnew;
+      gpos += wi.nnew;
     }
     c->st_iters = it + 1;
   }

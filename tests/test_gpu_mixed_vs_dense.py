@@ -2,8 +2,13 @@
 
 Dot 32/128/384 (ph dimension 4096, perturbative width): the dense oracle (M has 8192^2
 entries) still finishes in about a minute on the host.  Bars: FP64 form 1e-8 Ha, mixed form
-(BF16 tensor-core sigma, FP64 Krylov, split-BF16 refinement) 1e-6 Ha; oscillator strengths
-1e-4 relative for roots whose neighbours are at least 1e-5 Ha away.
+(BF16 tensor-core sigma, FP64 Krylov, split-BF16 refinement) 1e-6 Ha.  Oscillator strengths:
+1e-4 relative in the FP64 form for roots whose neighbours are at least 1e-5 Ha away.  In the
+mixed form the returned vector is an eigenvector of the reduced-precision operator; it mixes
+in the neighbouring root n by at most |r| / |omega - omega_n| (first-order perturbation
+theory), and f, quadratic in the vector, moves by at most twice that relative to sqrt(f f_n)
+per neighbour -- the test allows 1e-4 relative plus 4 |r| / gap times the larger f of the
+root and its nearest neighbour, gap taken over the whole spectrum.
 """
 
 import numpy as np
@@ -27,15 +32,24 @@ def case():
     return inp, ref, w0
 
 
-def _check(got, ref, w0, tol):
+def _check(got, ref, w0, tol, mixed=False):
     idx = po.select_window(ref["omega"], w0, 0.1, 8, select=0)
     assert len(got["omega"]) == len(idx)
     np.testing.assert_allclose(got["omega"], ref["omega"][idx], atol=tol, rtol=0)
-    w = ref["omega"][idx]
-    for i in range(len(w)):
-        gap = min([abs(w[i] - w[j]) for j in range(len(w)) if j != i] + [1.0])
-        if gap > 1e-5:
-            assert abs(got["osc"][i] - ref["f"][idx][i]) <= 1e-4 * max(abs(ref["f"][idx][i]), 1e-3)
+    allw = ref["omega"]
+    for i, n in enumerate(idx):
+        d = np.abs(allw - allw[n])
+        d[n] = np.inf
+        nb = int(np.argmin(d))
+        gap = d[nb]
+        if gap <= 1e-5:
+            continue
+        f = ref["f"][n]
+        if mixed:
+            scale = max(abs(f), abs(ref["f"][nb]), 1e-3)
+            assert abs(got["osc"][i] - f) <= 1e-4 * max(abs(f), 1e-3) + 4.0 * got["resid"][i] / gap * scale
+        else:
+            assert abs(got["osc"][i] - f) <= 1e-4 * max(abs(f), 1e-3)
 
 
 def test_fp64_form_matches_dense(cuda_lib, case):
@@ -57,4 +71,5 @@ def test_mixed_form_matches_dense(cuda_lib, case):
         got = dot.solve_window(w0, 0.1, 8)
     finally:
         dot.close()
-    _check(got, ref, w0, 1e-6)
+    assert np.all(got["resid"] <= 1e-6)
+    _check(got, ref, w0, 1e-6, mixed=True)
