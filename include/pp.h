@@ -115,6 +115,33 @@ pp_status pp_sigma(pp_ctx *ctx, int nvec, const double *Z, double *sigma, double
                    int prec, int on_device);
 
 /*
+ * Allocation-free metric product: out = Sigma z for nvec supervectors, the same
+ * product as pp_sigma's metric output (Sigma = diag(S, -S), S = 1 + S(2) as above),
+ * computed in FP64.  The paper has no counterpart to this entry point: it serves
+ * callers that must not allocate device memory when they need the product -- code
+ * running inside another framework's device memory pool (a raw cudaMalloc/cudaFree
+ * would escape the pool's budget and accounting) and latency-critical loops that
+ * avoid cudaMalloc/cudaFree because they can synchronise the device.  It calls
+ * neither, nor any allocating library routine.
+ *   Z, out: [nvec][2][nocc][nvir] doubles in DEVICE memory of the current device
+ *           (no host staging); Z and out must not overlap.
+ *   nvec * nocc * nvir must not exceed PP_METRIC_NOALLOC_MAX_ELEMS: the two
+ *           intermediate products live in one fixed 16 MiB array per device compiled
+ *           into the library.  Larger batches return PP_EINVAL with the sizes in
+ *           pp_last_error; split them, or use pp_sigma.
+ *   The array is shared by all contexts and calls on a device: calls that overlap in
+ *   time on one device (several host threads, or streams running concurrently) race
+ *   on it and may return wrong results, so serialise them.  Nothing in it needs to
+ *   start at zero.
+ *   Set-up: the first call on each device (nvec = 0 does only the set-up) looks the
+ *   array's address up with that device current; it can load the library's device
+ *   code, so it must precede any stream capture on that device.
+ * Runs on the context's stream and returns after that stream has finished the work.
+ */
+#define PP_METRIC_NOALLOC_MAX_ELEMS (1LL << 19)
+pp_status pp_metric_noalloc(pp_ctx *ctx, int nvec, const double *Z, double *out);
+
+/*
  * diag(A) and diag(S), each [nocc][nvir] host doubles: the Jacobi splitting D
  * of Sec. 2.5.2 (D = diag(M) - omega diag(Sigma)).
  */

@@ -27,7 +27,7 @@ STATUS_NAMES = {
 
 # every symbol declared in include/pp.h
 EXPORTS = (
-    "pp_default_options", "pp_create", "pp_sigma", "pp_diagonal", "pp_solve_window",
+    "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
     "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
     "pp_last_error",
 )
@@ -70,6 +70,8 @@ def load(path: str | None = None):
         lib.pp_create.restype = C.c_int
         lib.pp_sigma.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int]
         lib.pp_sigma.restype = C.c_int
+        lib.pp_metric_noalloc.argtypes = [vp, C.c_int, vp, vp]
+        lib.pp_metric_noalloc.restype = C.c_int
         lib.pp_diagonal.argtypes = [vp, _dp, _dp]
         lib.pp_diagonal.restype = C.c_int
         lib.pp_solve_window.argtypes = [vp, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, vp,
@@ -171,6 +173,30 @@ def pp_sigma(ctx, Z, prec: int = PP_FP64, metric: bool = False):
     return (sig, met) if metric else sig
 
 
+PP_METRIC_NOALLOC_MAX_ELEMS = 1 << 19
+
+
+def pp_metric_noalloc(ctx, Z, out):
+    """out = Sigma z without any device allocation in the library.
+
+    Z and out are CUDA float64 tensors [nvec, 2, nocc, nvir] that the caller owns
+    (nothing is allocated here either); nvec * nocc * nvir <= PP_METRIC_NOALLOC_MAX_ELEMS.
+    Calls that overlap in time on one device share the library's fixed scratch array
+    and must be serialised by the caller.
+    """
+    lib = load()
+    import torch
+
+    for t in (Z, out):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("pp_metric_noalloc needs contiguous CUDA float64 tensors")
+    if Z.shape != out.shape:
+        raise ValueError("Z and out must have the same shape")
+    st = lib.pp_metric_noalloc(ctx, int(Z.shape[0]), Z.data_ptr(), out.data_ptr())
+    _check(st, ctx)
+    return out
+
+
 def pp_diagonal(ctx, nocc: int, nvir: int):
     lib = load()
     dA = np.empty((nocc, nvir))
@@ -268,6 +294,9 @@ class Dot:
 
     def sigma(self, Z, prec=PP_FP64, metric=False):
         return pp_sigma(self.ctx, Z, prec, metric)
+
+    def metric_noalloc(self, Z, out):
+        return pp_metric_noalloc(self.ctx, Z, out)
 
     def diagonal(self):
         return pp_diagonal(self.ctx, self.nocc, self.nvir)
