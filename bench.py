@@ -357,7 +357,7 @@ def profile_workload(args):
             pp.pp_sigma(dot.ctx, Z, prec=pp.PP_BF16)
         torch.cuda.synchronize()
     else:
-        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=1e-7,
+        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL,
                      max_iter=args.profile_solve)
         dA, dS = dot.diagonal()
         omega0 = float(np.percentile((dA / dS).ravel(), w["pct"]))

@@ -98,8 +98,11 @@ void pp_default_options(pp_options *opt);
  *         symmetric in the last two indices (only the blocks oo, ov, vv are read)
  *   mu    [3][nocc][nvir]        dipole integrals, host (may be NULL: no oscillator strengths)
  * Computes the per-dot intermediates (MP2 densities and the 3-index ring
- * intermediate, the Jacobi diagonal) on the device.  Returns PP_EMETRIC if the
- * diagonal of S is not positive.
+ * intermediate, the Jacobi diagonal) on the device: in FP64 when opt->prec is
+ * PP_FP64, otherwise on the tensor cores (split-BF16 amplitudes, FP32 sums; relative
+ * error about 1e-6 in these second-order intermediates, which every later sigma of
+ * the context, FP64 ones included, inherits).  Returns PP_EMETRIC if the diagonal
+ * of S is not positive.
  */
 pp_status pp_create(int nocc, int nvir, int naux, const double *eps, const void *B, int B_dtype,
                     const double *mu, const pp_options *opt, pp_ctx **out);

@@ -2,7 +2,10 @@
 // host/device staging, and error translation: no exception crosses the ABI.
 #include "pp_internal.h"
 
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -124,6 +127,13 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
       PP_CUDA(cudaMemcpyAsync(c->mu.p, mu, sizeof(double) * 3 * c->ov, cudaMemcpyHostToDevice, s));
       c->has_mu = true;
     }
+    const char *log_env = std::getenv("PP_LOG");
+    const bool log_on = log_env && log_env[0] && log_env[0] != '0';
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    auto t0 = now();
     if (naux > 0) {
       DevBuf full;
       const size_t bytes = nB * (B_dtype == 0 ? sizeof(double) : sizeof(float));
@@ -139,8 +149,13 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
       c->opt.order = 0;
       build_residency(c, nullptr, nullptr);
     }
-    precompute_f64(c);
     PP_CUDA(cudaStreamSynchronize(s));
+    auto t1 = now();
+    if (c->opt.prec == PP_FP64 || c->opt.order < 2 || c->Q == 0) precompute_f64(c);
+    else precompute_tc(c);
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (log_on)
+      std::fprintf(stderr, "[pp] create: upload + residency %.1f ms, precompute %.1f ms\n", ms(t0, t1), ms(t1, now()));
     // the Jacobi diagonal of S must be positive (S positive definite needs it)
     std::vector<double> dS(c->ov);
     PP_CUDA(cudaMemcpy(dS.data(), c->diagS.p, sizeof(double) * c->ov, cudaMemcpyDeviceToHost));

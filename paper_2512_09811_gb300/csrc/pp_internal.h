@@ -138,7 +138,13 @@ struct pp_ctx {
 
 // sigma_f64.cu
 void build_residency(pp_ctx *c, const double *Bd, const float *Bf);
+// per-dot intermediates (MP2 pair sums p_oo, q_oo, p_vv, q_vv, ring intermediate Gamma, then
+// GB and the Jacobi diagonal): precompute_f64 in FP64; precompute_tc on the tensor cores
+// (split-BF16 amplitude slabs and Gamma, FP32 pair sums), both via begin / finish
+void precompute_begin(pp_ctx *c);
+void precompute_finish(pp_ctx *c);
 void precompute_f64(pp_ctx *c);
+void precompute_tc(pp_ctx *c);
 void sigma_f64(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d);
 // tc_gemm.cu
 void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split);

@@ -191,7 +191,8 @@ static void choose_chunks(pp_ctx *c) {
   c->slab_i = (int)std::max<long long>(1, std::min<long long>(si, o));
 }
 
-void precompute_f64(pp_ctx *c) {
+// chunk sizes, and the per-dot intermediates allocated and zeroed
+void precompute_begin(pp_ctx *c) {
   const int o = c->o, v = c->v, Q = c->Q;
   const long long ov = c->ov;
   cudaStream_t s = c->stream;
@@ -200,12 +201,19 @@ void precompute_f64(pp_ctx *c) {
   c->q_oo.ensure(sizeof(double) * o * o);
   c->p_vv.ensure(sizeof(double) * (size_t)v * v);
   c->q_vv.ensure(sizeof(double) * (size_t)v * v);
-  c->Gam.ensure(sizeof(double) * (size_t)Q * ov);
+  c->Gam.ensure(sizeof(double) * (size_t)std::max<long long>(1, Q * ov));
   PP_CUDA(cudaMemsetAsync(c->p_oo.p, 0, sizeof(double) * o * o, s));
   PP_CUDA(cudaMemsetAsync(c->q_oo.p, 0, sizeof(double) * o * o, s));
   PP_CUDA(cudaMemsetAsync(c->p_vv.p, 0, sizeof(double) * (size_t)v * v, s));
   PP_CUDA(cudaMemsetAsync(c->q_vv.p, 0, sizeof(double) * (size_t)v * v, s));
-  PP_CUDA(cudaMemsetAsync(c->Gam.p, 0, sizeof(double) * (size_t)Q * ov, s));
+  PP_CUDA(cudaMemsetAsync(c->Gam.p, 0, sizeof(double) * (size_t)std::max<long long>(1, Q * ov), s));
+}
+
+void precompute_f64(pp_ctx *c) {
+  const int o = c->o, v = c->v, Q = c->Q;
+  const long long ov = c->ov;
+  cudaStream_t s = c->stream;
+  precompute_begin(c);
   if (c->opt.order >= 2) {
     const int si = c->slab_i;
     c->w_T.ensure(sizeof(double) * (size_t)si * v * ov);
@@ -247,6 +255,14 @@ void precompute_f64(pp_ctx *c) {
     }
     c->w_Tw.release();
   }
+  precompute_finish(c);
+}
+
+// Bov + Gamma stacked over Bov for the exchange-type ring terms, and the Jacobi diagonal
+void precompute_finish(pp_ctx *c) {
+  const int o = c->o, v = c->v, Q = c->Q;
+  const long long ov = c->ov;
+  cudaStream_t s = c->stream;
   c->GB.ensure(sizeof(double) * 2 * (size_t)Q * ov);
   k_make_gb<<<ew_grid((long long)Q * ov), 256, 0, s>>>(c->GB.as<double>(), c->Bov.as<double>(),
                                                        c->Gam.as<double>(), (long long)Q * ov,

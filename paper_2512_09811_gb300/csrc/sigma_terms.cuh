@@ -88,13 +88,17 @@ __global__ void k_metric(double *__restrict__ met, const double *__restrict__ V,
   }
 }
 // sigma[s][0] = Aacc[2s] + Bacc[2s+1];  sigma[s][1] = Bacc[2s] + Aacc[2s+1]
+// (gap64 set: the diagonal term gap * V is added here in FP64 instead of living in Aacc)
 template <class T>
 __global__ void k_combine(double *__restrict__ sig, const T *__restrict__ Aacc,
-                          const T *__restrict__ Bacc, long long ov, long long total) {
+                          const T *__restrict__ Bacc, const double *__restrict__ gap64,
+                          const double *__restrict__ V64, long long ov, long long total) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
     long long r = p / ov, e = p % ov;
-    sig[p] = (double)Aacc[p] + (double)Bacc[(r ^ 1) * ov + e];
+    double x = (double)Aacc[p] + (double)Bacc[(r ^ 1) * ov + e];
+    if (gap64) x += gap64[e] * V64[p];
+    sig[p] = x;
   }
 }
 // FP32 sums may be split across blocks (atomic, order-dependent rounding); FP64 stays deterministic
@@ -116,8 +120,14 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
   T *Aacc = wk.Aacc, *Bacc = wk.Bacc;
   T *t1 = wk.tmp, *t2 = wk.tmp + (long long)R * ov, *t3 = wk.tmp + 2LL * R * ov, *t4 = wk.tmp + 3LL * R * ov;
   const long long tot = (long long)R * ov;
-  k_gap_scale<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, res.gap, V, ov, tot);
-  PP_LAUNCH_CHECK("k_gap_scale");
+  // reduced precision: the dominant diagonal term gap * V is added in FP64 by k_combine
+  const bool diag64 = sizeof(T) < sizeof(double);
+  if (diag64) {
+    PP_CUDA(cudaMemsetAsync(Aacc, 0, sizeof(T) * tot, s));
+  } else {
+    k_gap_scale<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, res.gap, V, ov, tot);
+    PP_LAUNCH_CHECK("k_gap_scale");
+  }
   PP_CUDA(cudaMemsetAsync(Bacc, 0, sizeof(T) * tot, s));
   if (order >= 1) {
     T *cq = wk.cq;
@@ -220,7 +230,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     k_a2<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, t1, t2, t3, t4, res.eps, o, v, tot);
     PP_LAUNCH_CHECK("k_a2");
   }
-  k_combine<T><<<ew_grid(tot), 256, 0, s>>>(sig, Aacc, Bacc, ov, tot);
+  k_combine<T><<<ew_grid(tot), 256, 0, s>>>(sig, Aacc, Bacc, diag64 ? c->gap.as<double>() : nullptr, V64, ov, tot);
   PP_LAUNCH_CHECK("k_combine");
   if (met) {
     k_metric<T><<<ew_grid(tot), 256, 0, s>>>(met, V64, t1, t3, order >= 2, ov, tot);

@@ -270,6 +270,8 @@ struct TgenArgs {
   const double *eps;
   __nv_bfloat16 *Thi, *Tlo;  // Tlo may be null
   long long ldT;
+  float *Tf;                  // optional FP32 copy [rows][ldf] (per-dot precompute)
+  long long ldf;
   int *err;
 };
 template <int STAGES>
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
     const double eij_c = (c < v) ? args.eps[i] + args.eps[j] - args.eps[o + c] : 0.0;
     __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + c) * args.ldT + (long long)j * v;
     __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + c) * args.ldT + (long long)j * v : nullptr;
+    float *frow = args.Tf ? args.Tf + ((long long)ii * v + c) * args.ldf + (long long)j * v : nullptr;
     for (int cc = 0; cc < BM; cc += 32) {
       float d1[32], d2[32];
       tmem_ld32(trow + cc, d1);
@@ -364,6 +367,7 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
             const __nv_bfloat16 h = __float2bfloat16_rn(t);
             hrow[d] = h;
             if (lrow) lrow[d] = __float2bfloat16_rn(t - __bfloat162float(h));
+            if (frow) frow[d] = t;
           }
         }
       }
@@ -422,6 +426,26 @@ __global__ void k_d2f(const double *__restrict__ s, float *__restrict__ d, long 
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x)
     d[p] = (float)s[p];
+}
+
+__global__ void k_f2d(const float *__restrict__ s, double *__restrict__ d, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    d[p] = (double)s[p];
+}
+// orbital-energy weights of the pair sums, FP32 slab T[(k,x)][(l,c)], k = i0 + row / v:
+// mode 0 (q_oo): e_k - e_x - e_c;  mode 1 (q_vv): e_k + e_l - e_c
+__global__ void k_weight_f32(float *__restrict__ Tw, const float *__restrict__ T, const double *__restrict__ eps,
+                             int o, int v, int i0, long long rows, int mode) {
+  const long long ov = (long long)o * v;
+  const long long total = rows * ov;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long row = p / ov, col = p % ov;
+    const int k = i0 + (int)(row / v), x = (int)(row % v), l = (int)(col / v), cc = (int)(col % v);
+    const double w = mode == 0 ? eps[k] - eps[o + x] - eps[o + cc] : eps[k] + eps[l] - eps[o + cc];
+    Tw[p] = T[p] * (float)w;
+  }
 }
 
 inline dim3 grid_for(long long n) {
@@ -495,7 +519,7 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
 
 void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq, long long ov, int o, int v,
           int i0, int ni, const double *eps, __nv_bfloat16 *Thi, __nv_bfloat16 *Tlo, long long ldT, int *err,
-          cudaStream_t s) {
+          cudaStream_t s, float *Tf = nullptr, long long ldf = 0) {
   static bool attr = false;
   if (!attr) {
     PP_CUDA(cudaFuncSetAttribute(k_tgen<TGEN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tgen_smem()));
@@ -506,7 +530,7 @@ void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq
   maps.hi = kmajor_map(bovT, ldq, ov, ldq, BM);
   maps.lo = bovT_lo ? kmajor_map(bovT_lo, ldq, ov, ldq, BM) : maps.hi;
   const int nt = (v + BM - 1) / BM;
-  TgenArgs a{o, v, (int)(ldq / BK), i0, nt, bovT_lo ? 3 : 1, eps, Thi, Tlo, ldT, err};
+  TgenArgs a{o, v, (int)(ldq / BK), i0, nt, bovT_lo ? 3 : 1, eps, Thi, Tlo, ldT, Tf, ldf, err};
   dim3 grid(nt * nt, o, ni);
   k_tgen<TGEN_STAGES><<<grid, 128, tgen_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_tgen");
@@ -527,6 +551,7 @@ struct KernelProfile {
 };
 struct TcPlan {
   long long ldq = 0, ldT = 0, vp = 0, Qp = 0;
+  bool ready = false;  // copies of the per-dot intermediates made (after the precompute)
   KernelProfile prof;
   int slab_i = 1, Rmax = 2;
   // BF16 hi/lo operands (K-major, K padded to 64)
@@ -609,7 +634,8 @@ static void bf16_pair(DevBuf &hi, DevBuf &lo, const double *src, long long rows,
 
 static long long pad64(long long x) { return std::max<long long>(tc::BK, ((x + tc::BK - 1) / tc::BK) * tc::BK); }
 
-static TcPlan *tc_plan(pp_ctx *c) {
+// Stage 1 of the plan: everything that depends on B and eps only (the precompute needs it).
+static TcPlan *tc_plan_operands(pp_ctx *c) {
   if (c->tc) return c->tc;
   TcPlan *p = new TcPlan();
   c->tc = p;
@@ -626,16 +652,9 @@ static TcPlan *tc_plan(pp_ctx *c) {
   f32_copy(p->f_Bvv, c->Bvv, Q * v * v, s);
   f32_copy(p->f_BvvP, c->BvvP, Q * v * v, s);
   f32_copy(p->f_BooT, c->BooT, Q * o * o, s);
-  f32_copy(p->f_GB, c->GB, 2 * Q * ov, s);
-  f32_copy(p->f_Gam, c->Gam, Q * ov, s);
-  f32_copy(p->f_poo, c->p_oo, o * o, s);
-  f32_copy(p->f_qoo, c->q_oo, o * o, s);
-  f32_copy(p->f_pvv, c->p_vv, v * v, s);
-  f32_copy(p->f_qvv, c->q_vv, v * v, s);
   if (c->opt.order >= 1 && Q > 0) {
     bf16_pair(p->bvv_hi, p->bvv_lo, c->Bvv.as<double>(), Q * v, v, v, p->vp, s);
     bf16_pair(p->bov_hi, p->bov_lo, c->Bov.as<double>(), Q * o, v, v, p->vp, s);
-    bf16_pair(p->gam_hi, p->gam_lo, c->Gam.as<double>(), Q * o, v, v, p->vp, s);
   }
   if (c->opt.order >= 2 && Q > 0) {
     p->bovT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
@@ -668,6 +687,118 @@ static TcPlan *tc_plan(pp_ctx *c) {
   p->err.ensure(sizeof(int) * 4);
   PP_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int) * 4, s));
   return p;
+}
+
+// Stage 2: FP32 / BF16 copies of the per-dot intermediates (made once the precompute is done).
+static TcPlan *tc_plan(pp_ctx *c) {
+  TcPlan *p = tc_plan_operands(c);
+  if (p->ready) return p;
+  const long long o = c->o, v = c->v, Q = c->Q, ov = c->ov;
+  cudaStream_t s = c->stream;
+  f32_copy(p->f_GB, c->GB, 2 * Q * ov, s);
+  f32_copy(p->f_Gam, c->Gam, Q * ov, s);
+  f32_copy(p->f_poo, c->p_oo, o * o, s);
+  f32_copy(p->f_qoo, c->q_oo, o * o, s);
+  f32_copy(p->f_pvv, c->p_vv, v * v, s);
+  f32_copy(p->f_qvv, c->q_vv, v * v, s);
+  if (c->opt.order >= 1 && Q > 0) bf16_pair(p->gam_hi, p->gam_lo, c->Gam.as<double>(), Q * o, v, v, p->vp, s);
+  p->ready = true;
+  return p;
+}
+
+static void throw_on_tc_error(TcPlan *p, cudaStream_t s) {
+  int herr = 0;
+  PP_CUDA(cudaMemcpyAsync(&herr, p->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    PP_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int), s));
+    throw PPError(PP_ETIMEOUT, "tensor-core kernel wait timed out (code " + std::to_string(herr) + ")");
+  }
+}
+
+// Per-dot intermediates on the tensor cores (contexts of the mixed form).  Amplitude slabs
+// T[(i,c)][(j,d)] = t_ij^cd come from the split-BF16 generator (FP32 accumulation, FP32 copy
+// of the slab); the pair sums (Eq. s(2) densities and the A(2) weights) are FP32 split-K
+// contractions of that copy; Gamma_Q[(i,c)] = sum_(j,d) t_ij^cd B_Q,jd is a split-BF16 GEMM.
+// The results (relative error about 1e-6) are stored in the FP64 context fields.
+void precompute_tc(pp_ctx *c) {
+  const int o = c->o, v = c->v, Q = c->Q;
+  const long long ov = c->ov;
+  cudaStream_t s = c->stream;
+  precompute_begin(c);
+  if (c->opt.order >= 2 && Q > 0) {
+    using bf = __nv_bfloat16;
+    TcPlan *p = tc_plan_operands(c);
+    const long long ldT = p->ldT;
+    const int si = p->slab_i;
+    p->t_hi.ensure(sizeof(bf) * (size_t)si * v * ldT);
+    p->t_lo.ensure(sizeof(bf) * (size_t)si * v * ldT);
+    DevBuf T32, Tw32, acc, bk_hi, bk_lo;
+    T32.ensure(sizeof(float) * (size_t)si * v * ov);
+    Tw32.ensure(sizeof(float) * (size_t)si * v * ov);
+    const long long nacc = 2LL * o * o + 2LL * v * v + (long long)Q * ov;
+    acc.ensure(sizeof(float) * (size_t)nacc);
+    PP_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(float) * (size_t)nacc, s));
+    float *poo = acc.as<float>(), *qoo = poo + o * o, *pvv = qoo + o * o, *qvv = pvv + (long long)v * v;
+    float *gam = qvv + (long long)v * v;
+    bf16_pair(bk_hi, bk_lo, c->Bov.as<double>(), Q, ov, ov, ldT, s);  // Bov as [Q][(j,d)], K-major
+    bf *thi = p->t_hi.as<bf>(), *tlo = p->t_lo.as<bf>();
+    float *T = T32.as<float>(), *Tw = Tw32.as<float>();
+    int *err = p->err.as<int>();
+    for (int i0 = 0; i0 < o; i0 += si) {
+      const int ni = std::min(si, o - i0);
+      const long long rows = (long long)ni * v;
+      if (ldT > ov) {
+        PP_CUDA(cudaMemset2DAsync(thi + ov, ldT * 2, 0, (ldT - ov) * 2, rows, s));
+        PP_CUDA(cudaMemset2DAsync(tlo + ov, ldT * 2, 0, (ldT - ov) * 2, rows, s));
+      }
+      tc::tgen(p->bovT_hi.as<bf>(), p->bovT_lo.as<bf>(), p->ldq, ov, o, v, i0, ni, c->eps.as<double>(), thi, tlo,
+               ldT, err, s, T, ov);
+      // p_oo[i][j] += sum_c sum_rho T[rho][(i,c)] T[rho][(j,c)]   (split over c)
+      GemmF32 g;
+      g.M = o; g.N = o; g.K = (int)rows; g.nred = v;
+      g.A = T; g.a_m = v; g.a_k = ov; g.a_red = 1;
+      g.B = T; g.b_k = ov; g.b_n = v; g.b_red = 1;
+      g.C = poo; g.c_m = o; g.c_n = 1; g.beta = 1.f;
+      g.ksplit = std::min(v, 256);
+      gemm_f32(g, s);
+      tc::k_weight_f32<<<tc::grid_for(rows * ov), 256, 0, s>>>(Tw, T, c->eps.as<double>(), o, v, i0, rows, 0);
+      PP_LAUNCH_CHECK("k_weight_f32");
+      g.B = Tw; g.C = qoo;
+      gemm_f32(g, s);
+      // p_vv[a][b] += sum_k sum_(l,c) T[(k,a)][(l,c)] T[(k,b)][(l,c)]   (split over k, else K)
+      GemmF32 h;
+      h.M = v; h.N = v; h.K = (int)ov; h.nred = ni;
+      h.A = T; h.a_m = ov; h.a_k = 1; h.a_red = (long long)v * ov;
+      h.B = T; h.b_k = 1; h.b_n = ov; h.b_red = (long long)v * ov;
+      h.C = pvv; h.c_m = v; h.c_n = 1; h.beta = 1.f;
+      h.ksplit = ni > 1 ? ni : 16;
+      gemm_f32(h, s);
+      tc::k_weight_f32<<<tc::grid_for(rows * ov), 256, 0, s>>>(Tw, T, c->eps.as<double>(), o, v, i0, rows, 1);
+      PP_LAUNCH_CHECK("k_weight_f32");
+      h.B = Tw; h.C = qvv;
+      gemm_f32(h, s);
+      // Gamma[Q][i0 v + row] = sum_(j,d) T[row][(j,d)] Bov[Q][(j,d)]
+      const bf *A[3] = {thi, thi, tlo};
+      const bf *B[3] = {bk_hi.as<bf>(), bk_lo.as<bf>(), bk_hi.as<bf>()};
+      tc::GemmOut out;
+      out.C = gam + (long long)i0 * v;
+      out.s_r0 = 1;
+      out.s_c0 = ov;
+      tc::gemm_bf16((int)rows, Q, ldT, 3, A, ldT, B, ldT, out, err, s);
+    }
+    const float *src[5] = {poo, qoo, pvv, qvv, gam};
+    double *dst[5] = {c->p_oo.as<double>(), c->q_oo.as<double>(), c->p_vv.as<double>(), c->q_vv.as<double>(),
+                      c->Gam.as<double>()};
+    const long long cnt[5] = {(long long)o * o, (long long)o * o, (long long)v * v, (long long)v * v,
+                              (long long)Q * ov};
+    for (int t = 0; t < 5; ++t) {
+      tc::k_f2d<<<tc::grid_for(cnt[t]), 256, 0, s>>>(src[t], dst[t], cnt[t]);
+      PP_LAUNCH_CHECK("k_f2d");
+    }
+    throw_on_tc_error(p, s);
+  }
+  precompute_finish(c);
 }
 
 static void ensure_zeroed(DevBuf &b, size_t bytes, cudaStream_t s) {
