@@ -283,12 +283,12 @@ extern "C" void pp_destroy(pp_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   tc_destroy(c);
+  if (c->wb) window_batch_destroy(c->wb);
+  c->wb = nullptr;
   DevBuf *bufs[] = {&c->eps, &c->gap, &c->Bov, &c->Boo, &c->Bvv, &c->BvvP, &c->BooT, &c->GB,
                     &c->Gam, &c->mu, &c->p_oo, &c->q_oo, &c->p_vv, &c->q_vv, &c->diagA,
                     &c->diagS, &c->w_acc, &c->w_cq, &c->w_W, &c->w_U, &c->w_P, &c->w_EF,
-                    &c->w_tmp, &c->w_T, &c->w_Tw, &c->w_V, &c->s_V, &c->s_MV, &c->s_SV,
-                    &c->s_X, &c->s_MX, &c->s_SX, &c->s_D, &c->s_MD, &c->s_SD, &c->s_G,
-                    &c->s_gram, &c->s_small, &c->s_part, &c->s_eig};
+                    &c->w_tmp, &c->w_T, &c->w_Tw, &c->w_V};
   for (DevBuf *b : bufs) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

@@ -43,10 +43,14 @@ extern unsigned long long g_pp_launches;
     if (e_ != cudaSuccess) throw PPError(PP_ECUDA, std::string(name) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// grow-only device buffer
+// grow-only device buffer (owns its allocation; not copyable)
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
   void ensure(size_t nbytes) {
     if (nbytes <= bytes) return;
     if (p) cudaFree(p);
@@ -103,6 +107,17 @@ void ew_copy_scale(double *y, const double *x, double a, long long n, cudaStream
 struct TcPlan;  // opaque
 
 // ---------------------------------------------------------------------------
+// window solver slots (solver.cu)
+// ---------------------------------------------------------------------------
+struct WindowBatch;  // opaque
+struct WindowResult {
+  int status = PP_OK;  // PP_OK or PP_ENOTCONV
+  int iters = 0;
+  std::vector<double> omega, osc, resid;  // nfound roots, ascending
+  std::vector<double> vecs;               // [nfound][2 ov] when vectors were requested
+};
+
+// ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
 struct pp_ctx {
@@ -126,8 +141,8 @@ struct pp_ctx {
   // BF16 tensor-core path (lazily built)
   TcPlan *tc = nullptr;
 
-  // solver workspaces
-  DevBuf s_V, s_MV, s_SV, s_X, s_MX, s_SX, s_D, s_MD, s_SD, s_G, s_gram, s_small, s_part, s_eig;
+  // window slots of the solver (lazily built, reused across pp_solve_window calls)
+  WindowBatch *wb = nullptr;
 
   // stats of the last solve
   int st_iters = 0;
@@ -152,5 +167,17 @@ void tc_destroy(pp_ctx *c);
 // solver.cu
 pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta, const int *k,
                              double *omega, double *osc, double *resid, double *vecs, int *nfound);
+// the context's cached slots with room for cap windows (rebuilt when too small or in use)
+WindowBatch *window_batch(pp_ctx *c, int cap, bool vectors);
+WindowBatch *window_batch_new(pp_ctx *c, int cap, bool vectors);  // owned by the caller
+void window_batch_destroy(WindowBatch *wb);
+int window_batch_add(WindowBatch *wb, double omega0, double delta, int k);  // slot, or -1 when full
+bool window_batch_has_work(const WindowBatch *wb);
+void window_batch_step(WindowBatch *wb);  // one iteration of every unfinished window
+bool window_batch_finished(const WindowBatch *wb, int slot);
+WindowResult window_batch_take(WindowBatch *wb, int slot);  // frees the slot
+void window_batch_release(WindowBatch *wb, int slot);       // frees the slot, result dropped
+int window_batch_capacity(const WindowBatch *wb);
+int window_batch_used(const WindowBatch *wb);
 // dispatch of one sigma application (solver and C ABI)
 void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec);

@@ -19,8 +19,12 @@
 //      inverse-Krylov direction is one weighted-Jacobi sweep (Sec. 2.5.2, the
 //      splitting M - theta Sigma = D + F) on the correction equation
 //      (M - theta Sigma) t = -r from t = 0, i.e. t = -D^-1 r;
-//   4. one sigma batch for all windows' directions, CGS2 against V (M V and
-//      Sigma V updated by the same combinations), thick restart when full.
+//   4. thick restart when the basis is full; the directions are orthonormalised
+//      against V (block CGS2) and among themselves (Cholesky QR twice), and the
+//      survivors of all windows are multiplied in one sigma batch per precision
+//      phase.
+// Windows live in the slots of a WindowBatch and advance one iteration per
+// step(); a window may join or leave between steps (the serving loop uses that).
 #include "pp_internal.h"
 
 #include <algorithm>
@@ -804,11 +808,17 @@ struct Solver {
 };
 
 struct Window {
+  bool used = false;     // slot holds a window
+  bool fresh = false;    // initial block not formed yet
+  bool finished = false; // results extracted, waiting to be taken
   double omega0 = 0, delta = 0;
   int k = 0;
   double shift = 0;
   int nev = 0, b = 0;
   int m = 0;
+  int prec = PP_FP64;    // precision phase of this window's sigma products
+  double tol = 0;        // residual tolerance of the current phase
+  int iters = 0;
   double *V = nullptr, *MV = nullptr, *SV = nullptr;  // [m_max][L]
   double *X = nullptr, *MX = nullptr, *SX = nullptr;  // [64][L]
   double *Vr = nullptr, *MVr = nullptr, *SVr = nullptr;  // [32][L] reduced blocks for the folded step
@@ -818,12 +828,15 @@ struct Window {
   std::vector<double> h_theta, h_res, h_xsx;
   std::vector<int> order;   // Ritz columns sorted by distance of theta to the shift
   std::vector<int> active;  // columns that get a direction this iteration
-  int nnew = 0;             // orthonormal new basis vectors staged for this iteration's sigma
+  int ndir = 0;             // directions staged for this step
+  long long dpos = 0;       // their first column in the direction buffer
+  int nnew = 0;             // orthonormal new basis vectors staged for this step's sigma
+  long long npos = 0;       // their first column in the direction buffer after compaction
   int bx = 0;               // block size of the last extraction (rows of Cref, columns of X)
-  bool done = false;
   int adjust = 0;
   double best_worst = 1e300;  // BF16 phase: best worst-residual seen, and iterations without gain
   int stall = 0;
+  WindowResult res;
 };
 
 }  // namespace
@@ -834,64 +847,62 @@ void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *m
   else sigma_bf16(c, nvec, Zd, sig_d, met_d, prec == PP_BF16X3);
 }
 
-pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta,
-                             const int *kk, double *omega_out, double *osc_out, double *resid_out,
-                             double *vecs_out, int *nfound) {
-  cudaStream_t s = c->stream;
-  const long long ov = c->ov, L = 2 * ov;
-  const int prec = c->opt.prec;
-  Solver sv{c, s, L};
-  const int m_max = std::min<int>(std::min(c->opt.m_max, MAXM), (int)L);
-  const int bcap = std::max(1, std::min(32, m_max / 3));
-  std::vector<double> hA(ov), hS(ov);
-  PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
-  PP_CUDA(cudaMemcpyAsync(hS.data(), c->diagS.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
-  PP_CUDA(cudaStreamSynchronize(s));
-  std::vector<double> ratio(ov);
-  for (long long p = 0; p < ov; ++p) ratio[p] = hA[p] / hS[p];
+// ---------------------------------------------------------------------------
+// WindowBatch: a fixed number of window slots of one context, advanced together one
+// iteration at a time.  Windows join (add) and leave (take) between steps; every step
+// forms the new vectors of all windows and multiplies them in at most two sigma batches
+// (one per precision phase).
+// ---------------------------------------------------------------------------
+struct WindowBatch {
+  pp_ctx *c;
+  cudaStream_t s;
+  long long ov, L;
+  int cap;
+  bool keep_vectors;
+  int m_max, bcap;
+  size_t vecbytes, per_win;
+  Solver sv;
+  std::vector<double> ratio;  // diag(A) / diag(S)
+  std::vector<Window> W;
+  DevBuf mem, D, MD, SD, part, small;
+  double *scratch = nullptr;
+  int *iscratch = nullptr;
+  bool log_on = false;
+  long long steps = 0;
+  bool refine = false;
+  int prec0 = PP_FP64;
 
-  std::vector<Window> W(nwin);
-  for (int w = 0; w < nwin; ++w) {
-    Window &wi = W[w];
-    wi.omega0 = omega0[w];
-    wi.delta = delta ? delta[w] : 0.0;
-    wi.k = kk[w];
-    if (wi.k <= 0) throw PPError(PP_EINVAL, "k must be positive");
-    if (c->opt.select == 1) {
-      wi.shift = wi.omega0;
-      wi.nev = wi.k + 2;
-    } else {
-      // centre the targets on the expected k lowest roots above omega0 (diagonal estimate)
-      std::vector<double> above;
-      for (long long p = 0; p < ov; ++p)
-        if (ratio[p] >= wi.omega0) above.push_back(ratio[p]);
-      std::sort(above.begin(), above.end());
-      double rk = above.empty() ? wi.omega0 : above[std::min<size_t>(above.size() - 1, wi.k - 1)];
-      wi.shift = wi.omega0 + 0.5 * (rk - wi.omega0);
-      wi.nev = wi.k + std::max(2, wi.k / 2);
-    }
-    wi.nev = std::min<int>(wi.nev, (int)L);
-    wi.b = std::min(bcap, std::max(wi.nev + 2, c->opt.block));
-    wi.b = std::min<int>(wi.b, (int)L);
-    wi.nev = std::min(wi.nev, wi.b);
-  }
-  // device memory: per window basis (3 m_max vectors), Ritz block (3 x 64), small matrices
-  const size_t vecbytes = sizeof(double) * (size_t)L;
-  const size_t mm = (size_t)MAXM * MAXM;
-  const size_t per_win = vecbytes * (3 * (size_t)m_max + 3 * 64 + 3 * 32) + sizeof(double) * 26 * mm + 64;
-  c->s_V.ensure(per_win * nwin);
-  c->s_D.ensure(vecbytes * 32 * nwin);
-  c->s_MD.ensure(vecbytes * 32 * nwin);
-  c->s_SD.ensure(vecbytes * 32 * nwin);
-  sv.part_elems = (size_t)296 * mm;
-  c->s_part.ensure(sizeof(double) * sv.part_elems);
-  sv.part = c->s_part.as<double>();
-  c->s_small.ensure(sizeof(double) * 8192);
-  double *scratch = c->s_small.as<double>();
-  int *iscratch = reinterpret_cast<int *>(scratch + 4096);
-  {
-    char *base = c->s_V.as<char>();
-    for (int w = 0; w < nwin; ++w) {
+  WindowBatch(pp_ctx *ctx, int capacity, bool vectors)
+      : c(ctx), s(ctx->stream), ov(ctx->ov), L(2 * ctx->ov), cap(capacity), keep_vectors(vectors),
+        sv{ctx, ctx->stream, 2 * ctx->ov} {
+    m_max = std::min<int>(std::min(c->opt.m_max, MAXM), (int)L);
+    bcap = std::max(1, std::min(32, m_max / 3));
+    prec0 = c->opt.prec;
+    refine = (prec0 == PP_BF16) && c->opt.refine;
+    std::vector<double> hA(ov), hS(ov);
+    PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaMemcpyAsync(hS.data(), c->diagS.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    ratio.resize(ov);
+    for (long long p = 0; p < ov; ++p) ratio[p] = hA[p] / hS[p];
+    // device memory: per window basis (3 m_max vectors), Ritz block (3 x 64), reduced blocks
+    // (3 x 32), small matrices; direction buffers of 32 columns per window
+    vecbytes = sizeof(double) * (size_t)L;
+    const size_t mm = (size_t)MAXM * MAXM;
+    per_win = vecbytes * (3 * (size_t)m_max + 3 * 64 + 3 * 32) + sizeof(double) * 26 * mm + 64;
+    mem.ensure(per_win * cap);
+    D.ensure(vecbytes * 32 * cap);
+    MD.ensure(vecbytes * 32 * cap);
+    SD.ensure(vecbytes * 32 * cap);
+    sv.part_elems = (size_t)296 * mm;
+    part.ensure(sizeof(double) * sv.part_elems);
+    sv.part = part.as<double>();
+    small.ensure(sizeof(double) * 8192);
+    scratch = small.as<double>();
+    iscratch = reinterpret_cast<int *>(scratch + 4096);
+    W.resize(cap);
+    char *base = mem.as<char>();
+    for (int w = 0; w < cap; ++w) {
       char *p = base + per_win * w;
       Window &wi = W[w];
       auto take = [&](size_t bytes) {
@@ -915,378 +926,104 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
       wi.dstat = (int *)take(sizeof(double) * mm);
       wi.dkept = wi.dstat + 4;
     }
-  }
-  const int ld = MAXM + 1;
-  const int smem_jac = 2 * MAXM * MAXM * (int)sizeof(double);
-  const int smem_chol = (MAXM * ld + MAXM) * (int)sizeof(double);
-  const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
-  PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
-  PP_CUDA(cudaFuncSetAttribute(k_chol_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
-  PP_CUDA(cudaFuncSetAttribute(k_refined, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ref));
-
-  cudaEvent_t e0 = c->ev0, e1 = c->ev1;
-  c->st_iters = 0;
-  c->st_sigvec = 0;
-  c->st_sigma_ms = 0.0;
-  float ms = 0.f;
-  // mixed precision: BF16 sigma to a loose tolerance, then the split form (FP32-level)
-  const bool refine = (prec == PP_BF16) && c->opt.refine;
-  int cur_prec = prec;
-  auto run_sigma = [&](int nv, const double *Z, double *Sg, double *Mt) {
-    PP_CUDA(cudaEventRecord(e0, s));
-    apply_sigma(c, nv, Z, Sg, Mt, cur_prec);
-    PP_CUDA(cudaEventRecord(e1, s));
-    PP_CUDA(cudaEventSynchronize(e1));
-    PP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    c->st_sigma_ms += ms;
-    c->st_sigvec += nv;
-  };
-
-  // ---- initial blocks: unit vectors on the diagonal entries nearest each shift
-  {
-    int off = 0;
-    std::vector<int> hidx;
-    for (int w = 0; w < nwin; ++w) {
-      Window &wi = W[w];
-      std::vector<long long> order(ov);
-      std::iota(order.begin(), order.end(), 0);
-      const long long nb = std::min<long long>(wi.b, ov);
-      std::partial_sort(order.begin(), order.begin() + nb, order.end(), [&](long long a, long long b2) {
-        double da = fabs(ratio[a] - wi.shift), db = fabs(ratio[b2] - wi.shift);
-        return da < db || (da == db && a < b2);
-      });
-      for (int j = 0; j < wi.b; ++j) hidx.push_back((int)(j < nb ? order[j] : ov + order[j - nb]));
-      off += wi.b;
-    }
-    PP_CUDA(cudaMemcpyAsync(iscratch, hidx.data(), sizeof(int) * hidx.size(), cudaMemcpyHostToDevice, s));
-    double *D = c->s_D.as<double>();
-    k_unit_vectors<<<dim3(64, off), 256, 0, s>>>(D, L, iscratch, off);
-    PP_LAUNCH_CHECK("k_unit_vectors");
-    run_sigma(off, D, c->s_MD.as<double>(), c->s_SD.as<double>());
-    off = 0;
-    for (int w = 0; w < nwin; ++w) {
-      Window &wi = W[w];
-      PP_CUDA(cudaMemcpyAsync(wi.V, D + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(wi.MV, c->s_MD.as<double>() + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(wi.SV, c->s_SD.as<double>() + (long long)off * L, vecbytes * wi.b, cudaMemcpyDeviceToDevice, s));
-      wi.m = wi.b;
-      off += wi.b;
-    }
+    const int ld = MAXM + 1;
+    const int smem_jac = 2 * MAXM * MAXM * (int)sizeof(double);
+    const int smem_chol = (MAXM * ld + MAXM) * (int)sizeof(double);
+    const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
+    PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
+    PP_CUDA(cudaFuncSetAttribute(k_chol_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
+    PP_CUDA(cudaFuncSetAttribute(k_refined, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ref));
+    const char *log_env = std::getenv("PP_LOG");
+    log_on = log_env && log_env[0] && log_env[0] != '0';
   }
 
-  const int max_iter = std::max(1, c->opt.max_iter);
-  const double tol_final = c->opt.res_tol;
-  double tol = refine ? std::max(tol_final, 1e-5) : tol_final;
-  const char *log_env = std::getenv("PP_LOG");
-  const bool log_on = log_env && log_env[0] && log_env[0] != '0';
-  pp_status fail = PP_OK;
-  bool all_done = false;
-  for (int it = 0; it < max_iter && !all_done && fail == PP_OK; ++it) {
-    all_done = true;
-    int off = 0;
-    for (int w = 0; w < nwin; ++w) {
-      Window &wi = W[w];
-      if (wi.done) continue;
-      const int m = wi.m;
-      const int b = std::min(wi.b, m);
-      wi.bx = b;
-      // Rayleigh-Ritz on the projected pencil (full basis)
-      sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
-      sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
-      PP_CUDA(cudaMemsetAsync(wi.dstat, 0, sizeof(int) * 4, s));
-      k_chol_rr<<<1, 256, (m * (m + 1) + m) * sizeof(double), s>>>(wi.Hm, wi.Hs, m, wi.Lm, wi.Yw, wi.Cw, wi.dstat);
-      PP_LAUNCH_CHECK("k_chol_rr");
-      int mp = (m + 1) & ~1;
-      k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
-      PP_LAUNCH_CHECK("k_jacobi_eig");
-      const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
-      k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);
-      PP_LAUNCH_CHECK("k_rr_select");
-      // folded step in the span of the nr Rayleigh-Ritz vectors nearest the shift: orthonormal
-      // coefficients Qr, reduced blocks V Qr^T, M V Qr^T, Sigma V Qr^T, and their small Grams
-      const int nr = std::min(nsel, 32);
-      k_mgs<<<1, 128, 0, s>>>(wi.Esel, m, nsel, nr, wi.Qr, wi.dkept, 0.0);
-      PP_LAUNCH_CHECK("k_mgs");
-      sv.combine(wi.V, m, wi.Qr, m, nr, wi.Vr, 1.0, 0.0);
-      sv.combine(wi.MV, m, wi.Qr, m, nr, wi.MVr, 1.0, 0.0);
-      sv.combine(wi.SV, m, wi.Qr, m, nr, wi.SVr, 1.0, 0.0);
-      sv.gram(wi.Vr, L, nr, wi.MVr, L, nr, wi.hm, nr);
-      sv.gram(wi.Vr, L, nr, wi.SVr, L, nr, wi.hs, nr);
-      sv.gram(wi.MVr, L, nr, wi.MVr, L, nr, wi.Gmm, nr);
-      sv.gram(wi.MVr, L, nr, wi.SVr, L, nr, wi.Gms, nr);
-      sv.gram(wi.SVr, L, nr, wi.SVr, L, nr, wi.Gss, nr);
-      {  // initial guesses in reduced coordinates: C0[j][p] = Esel_j . Qr_p
-        GemmF64 g;
-        g.M = b; g.N = nr; g.K = m;
-        g.A = wi.Esel; g.a_m = m; g.a_k = 1;
-        g.B = wi.Qr; g.b_k = 1; g.b_n = m;
-        g.C = wi.C0; g.c_m = nr; g.c_n = 1;
-        gemm_f64(g, s);
-      }
-      k_refined<<<1, 256, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
-          wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
-      PP_LAUNCH_CHECK("k_refined");
-      sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);
-      sv.combine(wi.MVr, nr, wi.Cred, nr, b, wi.MX, 1.0, 0.0);
-      sv.combine(wi.SVr, nr, wi.Cred, nr, b, wi.SX, 1.0, 0.0);
-      {  // coefficients of the folded vectors in the full basis (thick restart): Cref = Cred Qr
-        GemmF64 g;
-        g.M = b; g.N = m; g.K = nr;
-        g.A = wi.Cred; g.a_m = nr; g.a_k = 1;
-        g.B = wi.Qr; g.b_k = m; g.b_n = 1;
-        g.C = wi.Cref; g.c_m = m; g.c_n = 1;
-        gemm_f64(g, s);
-      }
-      double *dots = scratch;  // [b][3]
-      double *theta_d = scratch + 3 * 64;
-      double *rn = scratch + 4 * 64;
-      k_ritz_dots<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, L, dots);
-      PP_LAUNCH_CHECK("k_ritz_dots");
-      std::vector<double> hd(3 * b);
-      int hstat[4];
-      PP_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 3 * b, cudaMemcpyDeviceToHost, s));
-      PP_CUDA(cudaMemcpyAsync(hstat, wi.dstat, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-      PP_CUDA(cudaStreamSynchronize(s));
-      if (hstat[0] == 1) {
-        fail = PP_EUNSTABLE;  // V^T M V not positive definite: M is not positive definite
-        c->err = "projected M is not positive definite (unstable RPA problem)";
+  int used() const {
+    int n = 0;
+    for (const Window &wi : W) n += wi.used ? 1 : 0;
+    return n;
+  }
+  bool has_work() const {
+    for (const Window &wi : W)
+      if (wi.used && !wi.finished) return true;
+    return false;
+  }
+
+  // A new window in a free slot (-1 if none).  Its initial block is formed by the next step.
+  int add(double omega0, double delta, int k) {
+    if (k <= 0) throw PPError(PP_EINVAL, "k must be positive");
+    if (k > 24) throw PPError(PP_EINVAL, "k must be at most 24 per window");
+    int slot = -1;
+    for (int w = 0; w < cap; ++w)
+      if (!W[w].used) {
+        slot = w;
         break;
       }
-      wi.h_theta.assign(b, 0.0);
-      wi.h_xsx.assign(b, 0.0);
-      for (int j = 0; j < b; ++j) {
-        wi.h_xsx[j] = hd[3 * j + 1] / hd[3 * j + 2];
-        wi.h_theta[j] = hd[3 * j] / hd[3 * j + 1];
-      }
-      PP_CUDA(cudaMemcpyAsync(theta_d, wi.h_theta.data(), sizeof(double) * b, cudaMemcpyHostToDevice, s));
-      double *Dcols = c->s_D.as<double>() + (long long)off * L;
-      k_resid_dir<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, theta_d, c->diagA.as<double>(),
-                                    c->diagS.as<double>(), ov, c->opt.jacobi_floor, Dcols, rn);
-      PP_LAUNCH_CHECK("k_resid_dir");
-      std::vector<double> hr(b);
-      PP_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
-      PP_CUDA(cudaStreamSynchronize(s));
-      wi.h_res.assign(b, 0.0);
-      for (int j = 0; j < b; ++j) {
-        double nx2 = hd[3 * j + 2];
-        wi.h_res[j] = sqrt(hr[j] / nx2) / fabs(wi.h_xsx[j]);
-      }
-      wi.order.resize(b);
-      std::iota(wi.order.begin(), wi.order.end(), 0);
-      std::stable_sort(wi.order.begin(), wi.order.end(), [&](int a, int b2) {
-        return fabs(wi.h_theta[a] - wi.shift) < fabs(wi.h_theta[b2] - wi.shift);
-      });
-      // the roots this window needs: the k lowest targets inside [omega0, omega0 + delta]
-      // (select 0) or the k targets nearest omega0 (select 1); only they must meet the tolerance
-      std::vector<int> need;
-      if (c->opt.select == 1) {
-        for (int t = 0; t < b && (int)need.size() < wi.k; ++t) need.push_back(wi.order[t]);
-      } else {
-        std::vector<int> in;
-        for (int j = 0; j < b; ++j)
-          if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
-        std::sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
-        for (int j = 0; j < (int)in.size() && (int)need.size() < wi.k; ++j) need.push_back(in[j]);
-      }
-      bool conv = !need.empty();
-      double worst = 0.0;
-      for (int j : need) {
-        if (!(wi.h_res[j] <= tol)) conv = false;
-        worst = std::max(worst, wi.h_res[j]);
-      }
-      if (log_on) {
-        std::fprintf(stderr, "[pp] it %d win %d m %d b %d nev %d shift %.6f stat %d,%d worst %.2e |", it, w,
-                     m, b, wi.nev, wi.shift, hstat[0], hstat[1], worst);
-        for (int t = 0; t < wi.nev; ++t)
-          std::fprintf(stderr, " %.6f(%.1e)", wi.h_theta[wi.order[t]], wi.h_res[wi.order[t]]);
-        std::fprintf(stderr, "\n");
-      }
-      if (!conv && refine && cur_prec == PP_BF16) {
-        // the BF16 phase ends when its residuals stop improving: the rest is left to the split form
-        if (worst < 0.7 * wi.best_worst) {
-          wi.best_worst = worst;
-          wi.stall = 0;
-        } else if (++wi.stall >= 8) {
-          int below = 0;
-          for (int j : need)
-            if (wi.h_res[j] <= 1e-3) ++below;
-          if (!need.empty() && 2 * below >= (int)need.size()) conv = true;
-        }
-      }
-      if (conv) {
-        bool ok = true;
-        if (c->opt.select == 0) {
-          double tmin = 1e300, tmax = -1e300;
-          for (int j = 0; j < b; ++j) {
-            tmin = std::min(tmin, wi.h_theta[j]);
-            tmax = std::max(tmax, wi.h_theta[j]);
-          }
-          const bool low_covered = tmin <= wi.omega0;
-          const bool top_ok = ((int)need.size() >= wi.k) || (tmax >= wi.omega0 + wi.delta);
-          if (!low_covered) {
-            ok = false;  // targets do not reach down to omega0: move the centre down
-            wi.shift = std::max(wi.omega0, wi.shift - 0.5 * (tmin - wi.omega0) - 0.25 * (tmax - tmin));
-          } else if (!top_ok) {
-            ok = false;  // fewer than k in the window and the window is not covered: widen
-            if (wi.b < bcap) {
-              wi.nev = std::min(wi.nev + std::max(2, wi.k / 2), bcap - 2);
-              wi.b = std::min(bcap, std::max(wi.b, wi.nev + 2));
-            } else {
-              wi.shift += 0.5 * (tmax - wi.shift);
-            }
-          }
-          if (!ok && ++wi.adjust > 8) ok = true;  // report what has been found
-        }
-        if (ok) {
-          wi.done = true;
-          continue;
-        }
-      }
-      all_done = false;
-      wi.active.clear();
-      int nd = 0;
-      for (int j = 0; j < b; ++j) {
-        if (wi.h_res[j] <= tol) continue;
-        if (nd != j)
-          PP_CUDA(cudaMemcpyAsync(Dcols + (long long)nd * L, Dcols + (long long)j * L, vecbytes,
-                                  cudaMemcpyDeviceToDevice, s));
-        wi.active.push_back(j);
-        ++nd;
-      }
-      if (nd == 0) {
-        // every block column has converged but the window is not covered yet: widen with the
-        // next Rayleigh-Ritz vectors' residual directions on the following iteration
-        wi.b = std::min(bcap, wi.b + 2);
-      }
-      off += nd;
+    if (slot < 0) return -1;
+    Window &wi = W[slot];
+    wi.used = true;
+    wi.fresh = true;
+    wi.finished = false;
+    wi.omega0 = omega0;
+    wi.delta = delta;
+    wi.k = k;
+    wi.m = 0;
+    wi.iters = 0;
+    wi.adjust = 0;
+    wi.stall = 0;
+    wi.best_worst = 1e300;
+    wi.bx = 0;
+    wi.ndir = wi.nnew = 0;
+    wi.prec = prec0;
+    wi.tol = refine ? std::max(c->opt.res_tol, 1e-5) : c->opt.res_tol;
+    wi.res = WindowResult();
+    if (c->opt.select == 1) {
+      wi.shift = wi.omega0;
+      wi.nev = wi.k + 2;
+    } else {
+      // centre the targets on the expected k lowest roots above omega0 (diagonal estimate)
+      std::vector<double> above;
+      for (long long p = 0; p < ov; ++p)
+        if (ratio[p] >= wi.omega0) above.push_back(ratio[p]);
+      std::sort(above.begin(), above.end());
+      double rk = above.empty() ? wi.omega0 : above[std::min<size_t>(above.size() - 1, wi.k - 1)];
+      wi.shift = wi.omega0 + 0.5 * (rk - wi.omega0);
+      wi.nev = wi.k + std::max(2, wi.k / 2);
     }
-    if (fail != PP_OK) break;
-    if (all_done && refine && cur_prec == PP_BF16) {
-      // refinement: restart every window on its folded targets and the next Rayleigh-Ritz
-      // vectors, recompute their products with the split (FP32-level) tensor-core sigma
-      cur_prec = PP_BF16X3;
-      tol = tol_final;
-      all_done = false;
-      for (int w = 0; w < nwin; ++w) {
-        Window &wi = W[w];
-        const int m = wi.m, b = wi.bx;
-        const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
-        PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
-        PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
-                                cudaMemcpyDeviceToDevice, s));
-        const int nout = std::min(64, std::min(m, 2 * b));
-        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
-        PP_LAUNCH_CHECK("k_mgs");
-        int kept = 0;
-        PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PP_CUDA(cudaStreamSynchronize(s));
-        sv.combine(wi.V, m, wi.Qk, m, kept, wi.X, 1.0, 0.0);
-        PP_CUDA(cudaMemcpyAsync(wi.V, wi.X, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
-        run_sigma(kept, wi.V, wi.MV, wi.SV);
-        wi.m = kept;
-        wi.done = false;
-        wi.adjust = 0;
-        wi.stall = 0;
-        wi.best_worst = 1e300;
-      }
-      continue;
-    }
-    if (all_done) break;
-    if (off == 0) continue;
-    // Each window: thick restart when the basis would overflow, then block CGS2 of its new
-    // directions against the basis and Cholesky QR (twice) among them -- on the vectors
-    // alone.  Products are formed afterwards, of the orthonormal survivors: the part of a
-    // direction left after orthogonalisation can be orders of magnitude smaller than the
-    // direction, and differencing reduced-precision products would amplify their rounding
-    // by that ratio.  The survivors of all windows are packed at the front of s_D for one
-    // batched sigma.
-    int pos = 0, gpos = 0;
-    for (int w = 0; w < nwin; ++w) {
-      Window &wi = W[w];
-      wi.nnew = 0;
-      if (wi.done || wi.active.empty()) continue;
-      const int nd = (int)wi.active.size();
-      const int b = wi.bx;
-      if (wi.m + nd > m_max) {
-        // thick restart: keep the folded vectors and the next Rayleigh-Ritz vectors
-        const int keep = std::min(wi.m, std::max(2 * b, m_max - nd - b));
-        const int m = wi.m;
-        const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
-        PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
-        PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
-                                cudaMemcpyDeviceToDevice, s));
-        k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept, 1e-20);
-        PP_LAUNCH_CHECK("k_mgs");
-        int kept = 0;
-        PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PP_CUDA(cudaStreamSynchronize(s));
-        double *stage = wi.X + (long long)b * L;  // X is free after the directions: room for 64 - b
-        if (kept > 64 - b) kept = 64 - b;
-        sv.combine(wi.V, m, wi.Qk, m, kept, stage, 1.0, 0.0);
-        PP_CUDA(cudaMemcpyAsync(wi.V, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
-        sv.combine(wi.MV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
-        PP_CUDA(cudaMemcpyAsync(wi.MV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
-        sv.combine(wi.SV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
-        PP_CUDA(cudaMemcpyAsync(wi.SV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
-        wi.m = kept;
-      }
-      const int m0 = wi.m;
-      double *Nv = c->s_D.as<double>() + (long long)pos * L;
-      double *H = wi.Kc;   // [nd][m0]
-      double *GN = wi.Qk;  // [nd][nd]
-      double *Tq = wi.Yw;  // [nd][nd]
-      int *kflag = (int *)(scratch + 6144);
-      for (int pass = 0; pass < 2 && m0 > 0; ++pass) {
-        sv.gram(Nv, L, nd, wi.V, L, m0, H, m0);  // H[j][k] = N_j . V_k
-        sv.combine(wi.V, m0, H, m0, nd, Nv, -1.0, 1.0);
-      }
-      int nkeep = nd;
-      for (int qr = 0; qr < 2 && nkeep > 0; ++qr) {
-        sv.gram(Nv, L, nkeep, Nv, L, nkeep, GN, nkeep);
-        k_cholqr<<<1, 32, 0, s>>>(GN, nkeep, qr == 0 ? 1e-14 : 1e-10, Tq, kflag);
-        PP_LAUNCH_CHECK("k_cholqr");
-        std::vector<int> hk(nkeep);
-        PP_CUDA(cudaMemcpyAsync(hk.data(), kflag, sizeof(int) * nkeep, cudaMemcpyDeviceToHost, s));
-        PP_CUDA(cudaStreamSynchronize(s));
-        // orthonormalised block staged in X, the kept columns compacted back into place
-        sv.combine(Nv, nkeep, Tq, nkeep, nkeep, wi.X, 1.0, 0.0);
-        double *dst = (qr == 1) ? c->s_D.as<double>() + (long long)gpos * L : Nv;
-        int w2 = 0;
-        for (int j = 0; j < nkeep; ++j) {
-          if (!hk[j]) continue;
-          PP_CUDA(cudaMemcpyAsync(dst + (long long)w2 * L, wi.X + (long long)j * L, vecbytes,
-                                  cudaMemcpyDeviceToDevice, s));
-          ++w2;
-        }
-        nkeep = w2;
-      }
-      wi.nnew = nkeep;
-      gpos += nkeep;
-      pos += nd;
-    }
-    if (gpos > 0) run_sigma(gpos, c->s_D.as<double>(), c->s_MD.as<double>(), c->s_SD.as<double>());
-    gpos = 0;
-    for (int w = 0; w < nwin; ++w) {
-      Window &wi = W[w];
-      if (wi.nnew == 0) continue;
-      const long long at = (long long)wi.m * L, from = (long long)gpos * L;
-      PP_CUDA(cudaMemcpyAsync(wi.V + at, c->s_D.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(wi.MV + at, c->s_MD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
-      PP_CUDA(cudaMemcpyAsync(wi.SV + at, c->s_SD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
-      wi.m += wi.nnew;
-      gpos += wi.nnew;
-    }
-    c->st_iters = it + 1;
+    wi.nev = std::min<int>(wi.nev, (int)L);
+    wi.b = std::min(bcap, std::max(wi.nev + 2, c->opt.block));
+    wi.b = std::min<int>(wi.b, (int)L);
+    wi.nev = std::min(wi.nev, wi.b);
+    return slot;
   }
-  if (fail != PP_OK) return fail;
 
-  // ---- outputs
-  int base = 0;
-  pp_status st = PP_OK;
-  double *D = c->s_D.as<double>();
-  for (int w = 0; w < nwin; ++w) {
-    Window &wi = W[w];
-    if (!wi.done) st = PP_ENOTCONV;
+  bool finished(int slot) const { return W[slot].used && W[slot].finished; }
+
+  WindowResult take(int slot) {
+    Window &wi = W[slot];
+    WindowResult r = std::move(wi.res);
+    wi.used = wi.fresh = wi.finished = false;
+    wi.res = WindowResult();
+    wi.m = wi.ndir = wi.nnew = 0;
+    return r;
+  }
+
+  void timed_sigma(int nv, const double *Z, double *Sg, double *Mt, int prec) {
+    if (nv <= 0) return;
+    float ms = 0.f;
+    PP_CUDA(cudaEventRecord(c->ev0, s));
+    apply_sigma(c, nv, Z, Sg, Mt, prec);
+    PP_CUDA(cudaEventRecord(c->ev1, s));
+    PP_CUDA(cudaEventSynchronize(c->ev1));
+    PP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->st_sigma_ms += ms;
+    c->st_sigvec += nv;
+  }
+
+  // results of a window from its last extraction (the selection rules of pp_solve_window)
+  void finalize(Window &wi, int status) {
+    WindowResult &r = wi.res;
+    r.status = status;
+    r.iters = wi.iters;
     const int nb = (int)wi.order.size();
     std::vector<int> sel;
     if (c->opt.select == 1) {
@@ -1307,41 +1044,458 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
     }
     std::stable_sort(sel.begin(), sel.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
     const int nf = (int)sel.size();
-    nfound[w] = nf;
+    r.omega.assign(nf, 0.0);
+    r.osc.assign(nf, 0.0);
+    r.resid.assign(nf, 0.0);
     if (nf > 0) {
-      std::vector<double> th(nf), xs(nf);
+      std::vector<double> xs(nf);
       for (int t = 0; t < nf; ++t) {
-        th[t] = wi.h_theta[sel[t]];
+        r.omega[t] = wi.h_theta[sel[t]];
+        r.resid[t] = wi.h_res[sel[t]];
         xs[t] = wi.h_xsx[sel[t]];
-        omega_out[base + t] = th[t];
-        resid_out[base + t] = wi.h_res[sel[t]];
       }
-      // X columns are unit vectors (V orthonormal, refined coefficients normalised)
+      // X columns are unit vectors (V orthonormal, refined coefficients normalised); the
+      // direction buffer past the staged columns is free at this point of a step
+      double *Dv = wi.Vr;  // reduced-block buffer of this window: 32 columns, free after extraction
       for (int t = 0; t < nf; ++t)
-        PP_CUDA(cudaMemcpyAsync(D + (long long)t * L, wi.X + (long long)sel[t] * L, vecbytes,
+        PP_CUDA(cudaMemcpyAsync(Dv + (long long)t * L, wi.X + (long long)sel[t] * L, vecbytes,
                                 cudaMemcpyDeviceToDevice, s));
       double *thd = scratch, *xsd = scratch + 64, *od = scratch + 128;
-      PP_CUDA(cudaMemcpyAsync(thd, th.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(thd, r.omega.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
       PP_CUDA(cudaMemcpyAsync(xsd, xs.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
       if (c->has_mu) {
-        k_osc<<<nf, 256, 0, s>>>(D, c->mu.as<double>(), ov, thd, xsd, od);
+        k_osc<<<nf, 256, 0, s>>>(Dv, c->mu.as<double>(), ov, thd, xsd, od);
         PP_LAUNCH_CHECK("k_osc");
-        PP_CUDA(cudaMemcpyAsync(osc_out + base, od, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
-      } else {
-        for (int t = 0; t < nf; ++t) osc_out[base + t] = 0.0;
+        PP_CUDA(cudaMemcpyAsync(r.osc.data(), od, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
       }
-      if (vecs_out) {
-        PP_CUDA(cudaMemcpyAsync(vecs_out + (long long)base * L, D, vecbytes * nf, cudaMemcpyDeviceToHost, s));
-        PP_CUDA(cudaStreamSynchronize(s));
+      if (keep_vectors) {
+        r.vecs.assign((size_t)nf * L, 0.0);
+        PP_CUDA(cudaMemcpyAsync(r.vecs.data(), Dv, vecbytes * nf, cudaMemcpyDeviceToHost, s));
+      }
+      PP_CUDA(cudaStreamSynchronize(s));
+      if (keep_vectors)
         for (int t = 0; t < nf; ++t) {
-          double sc = 1.0 / sqrt(fabs(xs[t]));
-          double *vv = vecs_out + (long long)(base + t) * L;
+          const double sc = 1.0 / sqrt(fabs(xs[t]));
+          double *vv = r.vecs.data() + (size_t)t * L;
           for (long long l = 0; l < L; ++l) vv[l] *= sc;
         }
+    }
+    wi.finished = true;
+  }
+
+  // Rayleigh-Ritz, folded extraction, residuals, convergence and window coverage of one
+  // window; stages its correction directions at column pos of D.  Returns the number staged.
+  int extract(int w, long long pos) {
+    Window &wi = W[w];
+    const int m = wi.m;
+    const int b = std::min(wi.b, m);
+    wi.bx = b;
+    // Rayleigh-Ritz on the projected pencil (full basis)
+    sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
+    sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
+    PP_CUDA(cudaMemsetAsync(wi.dstat, 0, sizeof(int) * 4, s));
+    k_chol_rr<<<1, 256, (m * (m + 1) + m) * sizeof(double), s>>>(wi.Hm, wi.Hs, m, wi.Lm, wi.Yw, wi.Cw, wi.dstat);
+    PP_LAUNCH_CHECK("k_chol_rr");
+    int mp = (m + 1) & ~1;
+    k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
+    PP_LAUNCH_CHECK("k_jacobi_eig");
+    const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+    k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);
+    PP_LAUNCH_CHECK("k_rr_select");
+    // folded step in the span of the nr Rayleigh-Ritz vectors nearest the shift: orthonormal
+    // coefficients Qr, reduced blocks V Qr^T, M V Qr^T, Sigma V Qr^T, and their small Grams
+    const int nr = std::min(nsel, 32);
+    k_mgs<<<1, 128, 0, s>>>(wi.Esel, m, nsel, nr, wi.Qr, wi.dkept, 0.0);
+    PP_LAUNCH_CHECK("k_mgs");
+    sv.combine(wi.V, m, wi.Qr, m, nr, wi.Vr, 1.0, 0.0);
+    sv.combine(wi.MV, m, wi.Qr, m, nr, wi.MVr, 1.0, 0.0);
+    sv.combine(wi.SV, m, wi.Qr, m, nr, wi.SVr, 1.0, 0.0);
+    sv.gram(wi.Vr, L, nr, wi.MVr, L, nr, wi.hm, nr);
+    sv.gram(wi.Vr, L, nr, wi.SVr, L, nr, wi.hs, nr);
+    sv.gram(wi.MVr, L, nr, wi.MVr, L, nr, wi.Gmm, nr);
+    sv.gram(wi.MVr, L, nr, wi.SVr, L, nr, wi.Gms, nr);
+    sv.gram(wi.SVr, L, nr, wi.SVr, L, nr, wi.Gss, nr);
+    {  // initial guesses in reduced coordinates: C0[j][p] = Esel_j . Qr_p
+      GemmF64 g;
+      g.M = b; g.N = nr; g.K = m;
+      g.A = wi.Esel; g.a_m = m; g.a_k = 1;
+      g.B = wi.Qr; g.b_k = 1; g.b_n = m;
+      g.C = wi.C0; g.c_m = nr; g.c_n = 1;
+      gemm_f64(g, s);
+    }
+    k_refined<<<1, 256, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
+        wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
+    PP_LAUNCH_CHECK("k_refined");
+    sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);
+    sv.combine(wi.MVr, nr, wi.Cred, nr, b, wi.MX, 1.0, 0.0);
+    sv.combine(wi.SVr, nr, wi.Cred, nr, b, wi.SX, 1.0, 0.0);
+    {  // coefficients of the folded vectors in the full basis (thick restart): Cref = Cred Qr
+      GemmF64 g;
+      g.M = b; g.N = m; g.K = nr;
+      g.A = wi.Cred; g.a_m = nr; g.a_k = 1;
+      g.B = wi.Qr; g.b_k = m; g.b_n = 1;
+      g.C = wi.Cref; g.c_m = m; g.c_n = 1;
+      gemm_f64(g, s);
+    }
+    double *dots = scratch;  // [b][3]
+    double *theta_d = scratch + 3 * 64;
+    double *rn = scratch + 4 * 64;
+    k_ritz_dots<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, L, dots);
+    PP_LAUNCH_CHECK("k_ritz_dots");
+    std::vector<double> hd(3 * b);
+    int hstat[4];
+    PP_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 3 * b, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaMemcpyAsync(hstat, wi.dstat, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (hstat[0] == 1)  // V^T M V not positive definite: M is not positive definite
+      throw PPError(PP_EUNSTABLE, "projected M is not positive definite (unstable RPA problem)");
+    wi.h_theta.assign(b, 0.0);
+    wi.h_xsx.assign(b, 0.0);
+    for (int j = 0; j < b; ++j) {
+      wi.h_xsx[j] = hd[3 * j + 1] / hd[3 * j + 2];
+      wi.h_theta[j] = hd[3 * j] / hd[3 * j + 1];
+    }
+    PP_CUDA(cudaMemcpyAsync(theta_d, wi.h_theta.data(), sizeof(double) * b, cudaMemcpyHostToDevice, s));
+    double *Dcols = D.as<double>() + pos * L;
+    k_resid_dir<<<b, 256, 0, s>>>(wi.X, wi.MX, wi.SX, theta_d, c->diagA.as<double>(), c->diagS.as<double>(), ov,
+                                  c->opt.jacobi_floor, Dcols, rn);
+    PP_LAUNCH_CHECK("k_resid_dir");
+    std::vector<double> hr(b);
+    PP_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    wi.h_res.assign(b, 0.0);
+    for (int j = 0; j < b; ++j) {
+      double nx2 = hd[3 * j + 2];
+      wi.h_res[j] = sqrt(hr[j] / nx2) / fabs(wi.h_xsx[j]);
+    }
+    wi.order.resize(b);
+    std::iota(wi.order.begin(), wi.order.end(), 0);
+    std::stable_sort(wi.order.begin(), wi.order.end(), [&](int a, int b2) {
+      return fabs(wi.h_theta[a] - wi.shift) < fabs(wi.h_theta[b2] - wi.shift);
+    });
+    ++wi.iters;
+    // the roots this window needs: the k lowest targets inside [omega0, omega0 + delta]
+    // (select 0) or the k targets nearest omega0 (select 1); only they must meet the tolerance
+    std::vector<int> need;
+    if (c->opt.select == 1) {
+      for (int t = 0; t < b && (int)need.size() < wi.k; ++t) need.push_back(wi.order[t]);
+    } else {
+      std::vector<int> in;
+      for (int j = 0; j < b; ++j)
+        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
+      std::sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
+      for (int j = 0; j < (int)in.size() && (int)need.size() < wi.k; ++j) need.push_back(in[j]);
+    }
+    bool conv = !need.empty();
+    double worst = 0.0;
+    for (int j : need) {
+      if (!(wi.h_res[j] <= wi.tol)) conv = false;
+      worst = std::max(worst, wi.h_res[j]);
+    }
+    if (log_on) {
+      std::fprintf(stderr, "[pp] it %d win %d m %d b %d nev %d prec %d shift %.6f stat %d,%d worst %.2e |",
+                   wi.iters - 1, w, m, b, wi.nev, wi.prec, wi.shift, hstat[0], hstat[1], worst);
+      for (int t = 0; t < wi.nev; ++t)
+        std::fprintf(stderr, " %.6f(%.1e)", wi.h_theta[wi.order[t]], wi.h_res[wi.order[t]]);
+      std::fprintf(stderr, "\n");
+    }
+    if (!conv && refine && wi.prec == PP_BF16) {
+      // the BF16 phase ends when its residuals stop improving: the rest is left to the split form
+      if (worst < 0.7 * wi.best_worst) {
+        wi.best_worst = worst;
+        wi.stall = 0;
+      } else if (++wi.stall >= 8) {
+        int below = 0;
+        for (int j : need)
+          if (wi.h_res[j] <= 1e-3) ++below;
+        if (!need.empty() && 2 * below >= (int)need.size()) conv = true;
       }
     }
+    if (conv) {
+      bool ok = true;
+      if (c->opt.select == 0) {
+        double tmin = 1e300, tmax = -1e300;
+        for (int j = 0; j < b; ++j) {
+          tmin = std::min(tmin, wi.h_theta[j]);
+          tmax = std::max(tmax, wi.h_theta[j]);
+        }
+        const bool low_covered = tmin <= wi.omega0;
+        const bool top_ok = ((int)need.size() >= wi.k) || (tmax >= wi.omega0 + wi.delta);
+        if (!low_covered) {
+          ok = false;  // targets do not reach down to omega0: move the centre down
+          wi.shift = std::max(wi.omega0, wi.shift - 0.5 * (tmin - wi.omega0) - 0.25 * (tmax - tmin));
+        } else if (!top_ok) {
+          ok = false;  // fewer than k in the window and the window is not covered: widen
+          if (wi.b < bcap) {
+            wi.nev = std::min(wi.nev + std::max(2, wi.k / 2), bcap - 2);
+            wi.b = std::min(bcap, std::max(wi.b, wi.nev + 2));
+          } else {
+            wi.shift += 0.5 * (tmax - wi.shift);
+          }
+        }
+        if (!ok && ++wi.adjust > 8) ok = true;  // report what has been found
+      }
+      if (ok) {
+        if (refine && wi.prec == PP_BF16) {
+          switch_to_split(wi);
+        } else {
+          finalize(wi, PP_OK);
+        }
+        return 0;
+      }
+    }
+    if (wi.iters >= std::max(1, c->opt.max_iter)) {
+      finalize(wi, PP_ENOTCONV);
+      return 0;
+    }
+    wi.active.clear();
+    int nd = 0;
+    for (int j = 0; j < b; ++j) {
+      if (wi.h_res[j] <= wi.tol) continue;
+      if (nd != j)
+        PP_CUDA(cudaMemcpyAsync(Dcols + (long long)nd * L, Dcols + (long long)j * L, vecbytes,
+                                cudaMemcpyDeviceToDevice, s));
+      wi.active.push_back(j);
+      ++nd;
+    }
+    if (nd == 0) {
+      // every block column has converged but the window is not covered yet: widen with the
+      // next Rayleigh-Ritz vectors' residual directions on the following iteration
+      wi.b = std::min(bcap, wi.b + 2);
+    }
+    return nd;
+  }
+
+  // refinement: restart the window on its folded targets and the next Rayleigh-Ritz vectors,
+  // recompute their products with the split (FP32-level) tensor-core sigma
+  void switch_to_split(Window &wi) {
+    const int m = wi.m, b = wi.bx;
+    const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+    PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
+    PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
+                            cudaMemcpyDeviceToDevice, s));
+    const int nout = std::min(64, std::min(m, 2 * b));
+    k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
+    PP_LAUNCH_CHECK("k_mgs");
+    int kept = 0;
+    PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
     PP_CUDA(cudaStreamSynchronize(s));
-    base += wi.k;
+    sv.combine(wi.V, m, wi.Qk, m, kept, wi.X, 1.0, 0.0);
+    PP_CUDA(cudaMemcpyAsync(wi.V, wi.X, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+    wi.prec = PP_BF16X3;
+    wi.tol = c->opt.res_tol;
+    timed_sigma(kept, wi.V, wi.MV, wi.SV, wi.prec);
+    wi.m = kept;
+    wi.adjust = 0;
+    wi.stall = 0;
+    wi.best_worst = 1e300;
+  }
+
+  // thick restart when the basis would overflow, then block CGS2 of the staged directions
+  // against the basis and Cholesky QR (twice) among them -- on the vectors alone; the
+  // orthonormal survivors are packed at column gpos of D.  Products are formed afterwards, of
+  // the survivors: the part of a direction left after orthogonalisation can be orders of
+  // magnitude smaller than the direction, and differencing reduced-precision products would
+  // amplify their rounding by that ratio.
+  int orthonormalise(Window &wi, long long gpos) {
+    const int nd = wi.ndir;
+    const int b = wi.bx;
+    if (wi.m + nd > m_max) {
+      // thick restart: keep the folded vectors and the next Rayleigh-Ritz vectors
+      const int keep = std::min(wi.m, std::max(2 * b, m_max - nd - b));
+      const int m = wi.m;
+      const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
+      PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
+                              cudaMemcpyDeviceToDevice, s));
+      k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept, 1e-20);
+      PP_LAUNCH_CHECK("k_mgs");
+      int kept = 0;
+      PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      double *stage = wi.X + (long long)b * L;  // X is free after the directions: room for 64 - b
+      if (kept > 64 - b) kept = 64 - b;
+      sv.combine(wi.V, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+      PP_CUDA(cudaMemcpyAsync(wi.V, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+      sv.combine(wi.MV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+      PP_CUDA(cudaMemcpyAsync(wi.MV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+      sv.combine(wi.SV, m, wi.Qk, m, kept, stage, 1.0, 0.0);
+      PP_CUDA(cudaMemcpyAsync(wi.SV, stage, vecbytes * kept, cudaMemcpyDeviceToDevice, s));
+      wi.m = kept;
+    }
+    const int m0 = wi.m;
+    double *Nv = D.as<double>() + wi.dpos * L;
+    double *H = wi.Kc;   // [nd][m0]
+    double *GN = wi.Qk;  // [nd][nd]
+    double *Tq = wi.Yw;  // [nd][nd]
+    int *kflag = (int *)(scratch + 6144);
+    for (int pass = 0; pass < 2 && m0 > 0; ++pass) {
+      sv.gram(Nv, L, nd, wi.V, L, m0, H, m0);  // H[j][k] = N_j . V_k
+      sv.combine(wi.V, m0, H, m0, nd, Nv, -1.0, 1.0);
+    }
+    int nkeep = nd;
+    for (int qr = 0; qr < 2 && nkeep > 0; ++qr) {
+      sv.gram(Nv, L, nkeep, Nv, L, nkeep, GN, nkeep);
+      k_cholqr<<<1, 32, 0, s>>>(GN, nkeep, qr == 0 ? 1e-14 : 1e-10, Tq, kflag);
+      PP_LAUNCH_CHECK("k_cholqr");
+      std::vector<int> hk(nkeep);
+      PP_CUDA(cudaMemcpyAsync(hk.data(), kflag, sizeof(int) * nkeep, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      // orthonormalised block staged in X, the kept columns compacted back into place
+      sv.combine(Nv, nkeep, Tq, nkeep, nkeep, wi.X, 1.0, 0.0);
+      double *dst = (qr == 1) ? D.as<double>() + gpos * L : Nv;
+      int w2 = 0;
+      for (int j = 0; j < nkeep; ++j) {
+        if (!hk[j]) continue;
+        PP_CUDA(cudaMemcpyAsync(dst + (long long)w2 * L, wi.X + (long long)j * L, vecbytes,
+                                cudaMemcpyDeviceToDevice, s));
+        ++w2;
+      }
+      nkeep = w2;
+    }
+    return nkeep;
+  }
+
+  // unit vectors on the diagonal entries nearest the shift, at column gpos of D
+  int initial_block(Window &wi, long long gpos) {
+    std::vector<long long> ord(ov);
+    std::iota(ord.begin(), ord.end(), 0);
+    const long long nb = std::min<long long>(wi.b, ov);
+    std::partial_sort(ord.begin(), ord.begin() + nb, ord.end(), [&](long long a, long long b2) {
+      double da = fabs(ratio[a] - wi.shift), db = fabs(ratio[b2] - wi.shift);
+      return da < db || (da == db && a < b2);
+    });
+    std::vector<int> hidx(wi.b);
+    for (int j = 0; j < wi.b; ++j) hidx[j] = (int)(j < nb ? ord[j] : ov + ord[j - nb]);
+    PP_CUDA(cudaMemcpyAsync(iscratch, hidx.data(), sizeof(int) * wi.b, cudaMemcpyHostToDevice, s));
+    k_unit_vectors<<<dim3(64, wi.b), 256, 0, s>>>(D.as<double>() + gpos * L, L, iscratch, wi.b);
+    PP_LAUNCH_CHECK("k_unit_vectors");
+    PP_CUDA(cudaStreamSynchronize(s));  // hidx is released on return
+    wi.fresh = false;
+    return wi.b;
+  }
+
+  // One iteration of every unfinished window.  New vectors are grouped by precision phase
+  // so that each group is one contiguous sigma batch.
+  void step() {
+    ++steps;
+    const int groups[2] = {prec0, PP_BF16X3};
+    const int ngroups = refine ? 2 : 1;
+    long long start[2] = {0, 0}, end[2] = {0, 0};
+    long long pos = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      const int gp = groups[g];
+      start[g] = pos;
+      // extraction and directions of the windows with a basis, staged from column pos
+      long long dpos = pos;
+      for (int w = 0; w < cap; ++w) {
+        Window &wi = W[w];
+        if (!wi.used || wi.finished || wi.fresh || wi.prec != gp) continue;
+        wi.ndir = 0;
+        wi.nnew = 0;
+        const int nd = extract(w, dpos);
+        if (wi.finished || wi.prec != gp) continue;  // finished, or moved to the split phase
+        wi.ndir = nd;
+        wi.dpos = dpos;
+        dpos += nd;
+      }
+      // restart / orthonormalise, survivors packed from column pos (never ahead of dpos)
+      long long gpos = pos;
+      for (int w = 0; w < cap; ++w) {
+        Window &wi = W[w];
+        if (!wi.used || wi.finished || wi.fresh || wi.prec != gp || wi.ndir == 0) continue;
+        wi.nnew = orthonormalise(wi, gpos);
+        wi.npos = gpos;
+        gpos += wi.nnew;
+      }
+      // fresh windows of this phase: their initial blocks, right after the survivors (every
+      // staged direction of the phase has been consumed by now)
+      for (int w = 0; w < cap; ++w) {
+        Window &wi = W[w];
+        if (!wi.used || wi.finished || !wi.fresh || wi.prec != gp) continue;
+        wi.nnew = initial_block(wi, gpos);
+        wi.npos = gpos;
+        wi.ndir = 0;
+        gpos += wi.nnew;
+      }
+      end[g] = gpos;
+      pos = gpos;
+    }
+    for (int g = 0; g < ngroups; ++g) {
+      const long long n = end[g] - start[g];
+      if (n > 0)
+        timed_sigma((int)n, D.as<double>() + start[g] * L, MD.as<double>() + start[g] * L,
+                    SD.as<double>() + start[g] * L, groups[g]);
+    }
+    for (int w = 0; w < cap; ++w) {
+      Window &wi = W[w];
+      if (!wi.used || wi.finished || wi.nnew == 0) continue;
+      const long long at = (long long)wi.m * L, from = wi.npos * L;
+      PP_CUDA(cudaMemcpyAsync(wi.V + at, D.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.MV + at, MD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      PP_CUDA(cudaMemcpyAsync(wi.SV + at, SD.as<double>() + from, vecbytes * wi.nnew, cudaMemcpyDeviceToDevice, s));
+      wi.m += wi.nnew;
+      wi.nnew = 0;
+      wi.ndir = 0;
+    }
+  }
+};
+
+WindowBatch *window_batch(pp_ctx *c, int cap, bool vectors) {
+  if (c->wb && (c->wb->cap < cap || c->wb->used() > 0)) {
+    delete c->wb;
+    c->wb = nullptr;
+  }
+  if (!c->wb) c->wb = new WindowBatch(c, cap, vectors);
+  c->wb->keep_vectors = vectors;
+  return c->wb;
+}
+WindowBatch *window_batch_new(pp_ctx *c, int cap, bool vectors) { return new WindowBatch(c, cap, vectors); }
+void window_batch_destroy(WindowBatch *wb) { delete wb; }
+void window_batch_release(WindowBatch *wb, int slot) { (void)wb->take(slot); }
+int window_batch_add(WindowBatch *wb, double omega0, double delta, int k) { return wb->add(omega0, delta, k); }
+bool window_batch_has_work(const WindowBatch *wb) { return wb->has_work(); }
+void window_batch_step(WindowBatch *wb) { wb->step(); }
+bool window_batch_finished(const WindowBatch *wb, int slot) { return wb->finished(slot); }
+WindowResult window_batch_take(WindowBatch *wb, int slot) { return wb->take(slot); }
+int window_batch_capacity(const WindowBatch *wb) { return wb->cap; }
+int window_batch_used(const WindowBatch *wb) { return wb->used(); }
+
+pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta,
+                             const int *kk, double *omega_out, double *osc_out, double *resid_out,
+                             double *vecs_out, int *nfound) {
+  c->st_iters = 0;
+  c->st_sigvec = 0;
+  c->st_sigma_ms = 0.0;
+  WindowBatch *wb = window_batch(c, nwin, vecs_out != nullptr);
+  std::vector<int> slot(nwin);
+  for (int w = 0; w < nwin; ++w) {
+    slot[w] = wb->add(omega0[w], delta ? delta[w] : 0.0, kk[w]);
+    if (slot[w] < 0) throw PPError(PP_ECUDA, "window slots exhausted");
+  }
+  const long long steps0 = wb->steps;
+  try {
+    while (wb->has_work()) wb->step();
+  } catch (...) {
+    for (int w = 0; w < nwin; ++w) wb->take(slot[w]);
+    throw;
+  }
+  c->st_iters = (int)(wb->steps - steps0);
+  pp_status st = PP_OK;
+  long long base = 0;
+  const long long L = 2 * c->ov;
+  for (int w = 0; w < nwin; ++w) {
+    WindowResult r = wb->take(slot[w]);
+    if (r.status != PP_OK) st = (pp_status)r.status;
+    const int nf = (int)r.omega.size();
+    nfound[w] = nf;
+    for (int t = 0; t < nf; ++t) {
+      omega_out[base + t] = r.omega[t];
+      osc_out[base + t] = r.osc[t];
+      resid_out[base + t] = r.resid[t];
+    }
+    if (vecs_out && nf > 0) std::memcpy(vecs_out + base * L, r.vecs.data(), sizeof(double) * (size_t)nf * L);
+    base += kk[w];
   }
   return st;
 }
