@@ -198,6 +198,64 @@ void pp_destroy(pp_ctx *ctx);
 /* One-line description of the last error on ctx (or of the last failed pp_create). */
 const char *pp_last_error(const pp_ctx *ctx);
 
+/* ------------------------------------------------------------------------------------
+ * Serving: window-solve requests for several dots, continuously batched on one GPU.
+ *
+ * Each dot is registered once (host copies of its inputs are kept).  A dot is made
+ * resident -- its context (Sec. 2.2 intermediates) and its window slots on the device --
+ * when a request for it is scheduled and its estimated device footprint fits hbm_budget
+ * next to the resident dots; idle resident dots are evicted, least recently used first,
+ * to make room, and a dot that still does not fit waits until one does.  Worker threads
+ * advance resident dots one solver iteration at a time (the Sec. 2.5 window solver of
+ * pp_solve_windows); before each iteration the dot's queued requests are admitted into
+ * free window slots, so a request that arrives while others are running joins their
+ * sigma batches at the next iteration, and a finished window frees its slot at once.
+ * Dots are stepped by different workers on their own streams, so their work overlaps on
+ * the device.  Each result equals the one pp_solve_window gives for the same request
+ * within the solver tolerance (the iteration path differs with the batch).
+ * ------------------------------------------------------------------------------------ */
+typedef struct pp_server pp_server;
+
+typedef struct {
+  long long submitted, completed, failed;  /* requests (completed includes PP_ENOTCONV) */
+  long long ctx_created, ctx_evicted;      /* dots made resident / evicted */
+  long long steps;                         /* solver iterations run (all dots) */
+  int max_concurrent_dots;                 /* most dots stepped at the same time */
+  int max_windows_per_step;                /* most windows advanced by one step of one dot */
+  int resident_dots;                       /* at the time of the call */
+  long long resident_bytes;                /* estimated / measured device bytes of resident dots */
+} pp_server_stats_t;
+
+/*
+ * hbm_budget: device bytes the resident dots may hold (an estimate per dot until it has
+ * run, then its measured allocations).  opt: solver options for every dot (opt->cuda_stream
+ * must be NULL: each dot gets its own stream; NULL = defaults).  slots_per_dot: windows a
+ * dot advances together (1..16).  nworkers: worker threads (0 = 4, at most 16).  The
+ * current device is the server's device.
+ */
+pp_status pp_server_create(size_t hbm_budget, const pp_options *opt, int slots_per_dot, int nworkers,
+                           pp_server **out);
+/* Register a dot (arguments as pp_create; inputs are copied).  *dot_id numbers dots from 0. */
+pp_status pp_server_add_dot(pp_server *srv, int nocc, int nvir, int naux, const double *eps, const void *B,
+                            int B_dtype, const double *mu, int *dot_id);
+/* Queue a window request (arguments as pp_solve_window, select rule from the options). */
+pp_status pp_server_submit(pp_server *srv, int dot_id, double omega0, double delta, int k,
+                           unsigned long long *req_id);
+/*
+ * Wait up to timeout_ms (0: poll, < 0: no limit) for a request.  Returns PP_ETIMEOUT while
+ * it is not finished (it stays queued or running).  Otherwise writes omega/osc/resid (arrays
+ * of the request's k; any may be NULL), *nfound, latency_ms[0] = finish - submit and
+ * latency_ms[1] = admission - submit (may be NULL), forgets the request and returns its
+ * status (PP_OK, PP_ENOTCONV, or the failure of its dot).
+ */
+pp_status pp_server_wait(pp_server *srv, unsigned long long req_id, int timeout_ms, double *omega,
+                         double *osc, double *resid, int *nfound, double *latency_ms);
+pp_status pp_server_stats(pp_server *srv, pp_server_stats_t *out);
+/* Message of the last failed request returned by pp_server_wait. */
+const char *pp_server_last_error(const pp_server *srv);
+/* Stop the workers and free every dot.  No other call on srv may run concurrently. */
+void pp_server_destroy(pp_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

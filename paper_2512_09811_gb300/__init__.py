@@ -29,7 +29,8 @@ STATUS_NAMES = {
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
     "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
-    "pp_last_error",
+    "pp_last_error", "pp_server_create", "pp_server_add_dot", "pp_server_submit", "pp_server_wait",
+    "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
 )
 
 
@@ -38,6 +39,15 @@ class pp_options(C.Structure):
         ("prec", C.c_int), ("order", C.c_int), ("block", C.c_int), ("m_max", C.c_int),
         ("max_iter", C.c_int), ("res_tol", C.c_double), ("jacobi_floor", C.c_double),
         ("select", C.c_int), ("refine", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class pp_server_stats_t(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+        ("ctx_created", C.c_longlong), ("ctx_evicted", C.c_longlong), ("steps", C.c_longlong),
+        ("max_concurrent_dots", C.c_int), ("max_windows_per_step", C.c_int), ("resident_dots", C.c_int),
+        ("resident_bytes", C.c_longlong),
     ]
 
 
@@ -94,6 +104,21 @@ def load(path: str | None = None):
         lib.pp_destroy.restype = None
         lib.pp_last_error.argtypes = [vp]
         lib.pp_last_error.restype = C.c_char_p
+        lib.pp_server_create.argtypes = [C.c_size_t, C.POINTER(pp_options), C.c_int, C.c_int, C.POINTER(vp)]
+        lib.pp_server_create.restype = C.c_int
+        lib.pp_server_add_dot.argtypes = [vp, C.c_int, C.c_int, C.c_int, _dp, vp, C.c_int, _dp,
+                                          C.POINTER(C.c_int)]
+        lib.pp_server_add_dot.restype = C.c_int
+        lib.pp_server_submit.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_ulonglong)]
+        lib.pp_server_submit.restype = C.c_int
+        lib.pp_server_wait.argtypes = [vp, C.c_ulonglong, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _dp]
+        lib.pp_server_wait.restype = C.c_int
+        lib.pp_server_stats.argtypes = [vp, C.POINTER(pp_server_stats_t)]
+        lib.pp_server_stats.restype = C.c_int
+        lib.pp_server_last_error.argtypes = [vp]
+        lib.pp_server_last_error.restype = C.c_char_p
+        lib.pp_server_destroy.argtypes = [vp]
+        lib.pp_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -314,6 +339,114 @@ class Dot:
         if self.ctx:
             pp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def pp_server_create(hbm_budget: int, opt: pp_options | None = None, slots_per_dot: int = 4, nworkers: int = 0):
+    lib = load()
+    if opt is None:
+        opt = pp_default_options()
+    out = C.c_void_p()
+    st = lib.pp_server_create(int(hbm_budget), C.byref(opt), int(slots_per_dot), int(nworkers), C.byref(out))
+    if st != PP_OK:
+        raise PPError(st, "pp_server_create failed")
+    return out.value
+
+
+def pp_server_add_dot(srv, nocc: int, nvir: int, naux: int, eps, B, mu=None) -> int:
+    lib = load()
+    eps = _f64(eps)
+    B = np.ascontiguousarray(B)
+    if B.dtype == np.float32:
+        bdt = 1
+    else:
+        B = _f64(B)
+        bdt = 0
+    mu_a = _f64(mu) if mu is not None else None
+    did = C.c_int()
+    st = lib.pp_server_add_dot(srv, nocc, nvir, naux, _ptr(eps), B.ctypes.data_as(C.c_void_p), bdt,
+                               _ptr(mu_a) if mu_a is not None else None, C.byref(did))
+    if st != PP_OK:
+        raise PPError(st, "pp_server_add_dot failed")
+    return did.value
+
+
+def pp_server_submit(srv, dot_id: int, omega0: float, delta: float, k: int) -> int:
+    rid = C.c_ulonglong()
+    st = load().pp_server_submit(srv, int(dot_id), float(omega0), float(delta), int(k), C.byref(rid))
+    if st != PP_OK:
+        raise PPError(st, "pp_server_submit failed")
+    return rid.value
+
+
+def pp_server_wait(srv, req_id: int, k: int, timeout_ms: int = -1, allow_notconv: bool = False):
+    """Returns None on PP_ETIMEOUT, else dict(omega, osc, resid, latency_ms, queue_ms, status)."""
+    lib = load()
+    om = np.zeros(k)
+    osc = np.zeros(k)
+    res = np.zeros(k)
+    lat = np.zeros(2)
+    nf = C.c_int(0)
+    st = lib.pp_server_wait(srv, C.c_ulonglong(req_id), int(timeout_ms), _ptr(om), _ptr(osc), _ptr(res),
+                            C.byref(nf), _ptr(lat))
+    if st == PP_ETIMEOUT:
+        return None
+    if st != PP_OK and not (allow_notconv and st == PP_ENOTCONV):
+        raise PPError(st, lib.pp_server_last_error(srv).decode(errors="replace"))
+    n = nf.value
+    return dict(omega=om[:n], osc=osc[:n], resid=res[:n], latency_ms=float(lat[0]), queue_ms=float(lat[1]),
+                status=st)
+
+
+def pp_server_stats(srv) -> dict:
+    stt = pp_server_stats_t()
+    _check(load().pp_server_stats(srv, C.byref(stt)))
+    return {name: getattr(stt, name) for name, _ in pp_server_stats_t._fields_}
+
+
+def pp_server_last_error(srv) -> str:
+    return load().pp_server_last_error(srv).decode(errors="replace")
+
+
+def pp_server_destroy(srv):
+    if srv:
+        load().pp_server_destroy(srv)
+
+
+class Server:
+    """Owning wrapper of a serving loop."""
+
+    def __init__(self, hbm_budget: int, slots_per_dot: int = 4, nworkers: int = 0, **opts):
+        self.opt = pp_default_options(**opts)
+        self.srv = pp_server_create(hbm_budget, self.opt, slots_per_dot, nworkers)
+        self.dims = {}
+
+    def add_dot(self, inp) -> int:
+        did = pp_server_add_dot(self.srv, inp.nocc, inp.nvir, inp.naux, inp.eps, inp.B, inp.mu)
+        self.dims[did] = (inp.nocc, inp.nvir)
+        return did
+
+    def submit(self, dot_id: int, omega0: float, delta: float, k: int) -> int:
+        return pp_server_submit(self.srv, dot_id, omega0, delta, k)
+
+    def wait(self, req_id: int, k: int, timeout_ms: int = -1, **kw):
+        return pp_server_wait(self.srv, req_id, k, timeout_ms, **kw)
+
+    def stats(self) -> dict:
+        return pp_server_stats(self.srv)
+
+    def close(self):
+        if self.srv:
+            pp_server_destroy(self.srv)
+            self.srv = None
 
     def __del__(self):
         try:

@@ -279,6 +279,16 @@ extern "C" pp_status pp_last_stats(const pp_ctx *c, int *iterations, long long *
   return PP_OK;
 }
 
+size_t ctx_device_bytes(const pp_ctx *c) {
+  const DevBuf *bufs[] = {&c->eps, &c->gap, &c->Bov, &c->Boo, &c->Bvv, &c->BvvP, &c->BooT, &c->GB,
+                          &c->Gam, &c->mu, &c->p_oo, &c->q_oo, &c->p_vv, &c->q_vv, &c->diagA,
+                          &c->diagS, &c->w_acc, &c->w_cq, &c->w_W, &c->w_U, &c->w_P, &c->w_EF,
+                          &c->w_tmp, &c->w_T, &c->w_Tw, &c->w_V};
+  size_t n = tc_plan_bytes(c) + (c->wb ? window_batch_bytes(c->wb) : 0);
+  for (const DevBuf *b : bufs) n += b->bytes;
+  return n;
+}
+
 extern "C" void pp_destroy(pp_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);

@@ -178,6 +178,10 @@ bool window_batch_finished(const WindowBatch *wb, int slot);
 WindowResult window_batch_take(WindowBatch *wb, int slot);  // frees the slot
 void window_batch_release(WindowBatch *wb, int slot);       // frees the slot, result dropped
 int window_batch_capacity(const WindowBatch *wb);
+size_t window_batch_bytes(const WindowBatch *wb);
+// device bytes held by the tensor-core plan (tc_gemm.cu) and by a whole context (capi.cu)
+size_t tc_plan_bytes(const pp_ctx *c);
+size_t ctx_device_bytes(const pp_ctx *c);
 int window_batch_used(const WindowBatch *wb);
 // dispatch of one sigma application (solver and C ABI)
 void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec);

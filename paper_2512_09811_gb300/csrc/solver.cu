@@ -836,6 +836,7 @@ struct Window {
   int adjust = 0;
   double best_worst = 1e300;  // BF16 phase: best worst-residual seen, and iterations without gain
   int stall = 0;
+  int guard_wait = 0;  // iterations spent waiting for guard targets only
   WindowResult res;
 };
 
@@ -970,6 +971,7 @@ struct WindowBatch {
     wi.iters = 0;
     wi.adjust = 0;
     wi.stall = 0;
+    wi.guard_wait = 0;
     wi.best_worst = 1e300;
     wi.bx = 0;
     wi.ndir = wi.nnew = 0;
@@ -1186,11 +1188,57 @@ struct WindowBatch {
       std::sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
       for (int j = 0; j < (int)in.size() && (int)need.size() < wi.k; ++j) need.push_back(in[j]);
     }
+    // select 0: keep the targets centred on the span [omega0, theta_k] of the roots the window
+    // needs (theta_k the k-th lowest Ritz value inside it), so that the k-th root sits well
+    // inside the target block rather than at its edge
+    if (c->opt.select == 0 && (int)need.size() >= wi.k) {
+      double thk = wi.omega0;
+      for (int j : need) thk = std::max(thk, wi.h_theta[j]);
+      wi.shift = 0.5 * (wi.omega0 + thk);
+    }
+    // guards: an unconverged target whose Ritz value, give or take three residuals, reaches
+    // the span of the selected roots may still converge to a root inside it, so it must meet
+    // the tolerance too before the window is reported (else roots can be missed)
+    const int nsel_need = (int)need.size();
+    if (nsel_need > 0) {
+      double lo, hi;
+      if (c->opt.select == 1) {
+        double dk = 0.0;
+        for (int j : need) dk = std::max(dk, fabs(wi.h_theta[j] - wi.omega0));
+        lo = wi.omega0 - dk;
+        hi = wi.omega0 + dk;
+      } else {
+        lo = wi.omega0;
+        hi = wi.omega0;
+        for (int j : need) hi = std::max(hi, wi.h_theta[j]);
+        if (nsel_need < wi.k) hi = wi.omega0 + wi.delta;
+      }
+      // (only targets on their way to convergence: interior Rayleigh-Ritz also yields spurious
+      // values with residuals of order 0.1 that never converge)
+      for (int j = 0; j < b; ++j) {
+        if (std::find(need.begin(), need.end(), j) != need.end()) continue;
+        if (!(wi.h_res[j] <= 1e3 * wi.tol)) continue;
+        const double r3 = 3.0 * wi.h_res[j];
+        if (wi.h_theta[j] + r3 >= lo && wi.h_theta[j] - r3 <= hi) need.push_back(j);
+      }
+    }
     bool conv = !need.empty();
+    bool conv_sel = nsel_need > 0;
     double worst = 0.0;
-    for (int j : need) {
-      if (!(wi.h_res[j] <= wi.tol)) conv = false;
+    for (int t = 0; t < (int)need.size(); ++t) {
+      const int j = need[t];
+      if (!(wi.h_res[j] <= wi.tol)) {
+        conv = false;
+        if (t < nsel_need) conv_sel = false;
+      }
       worst = std::max(worst, wi.h_res[j]);
+    }
+    // guards that stay unconverged for many iterations while the selected roots have
+    // converged are given up on
+    if (!conv && conv_sel) {
+      if (++wi.guard_wait > 20) conv = true;
+    } else {
+      wi.guard_wait = 0;
     }
     if (log_on) {
       std::fprintf(stderr, "[pp] it %d win %d m %d b %d nev %d prec %d shift %.6f stat %d,%d worst %.2e |",
@@ -1220,7 +1268,7 @@ struct WindowBatch {
           tmax = std::max(tmax, wi.h_theta[j]);
         }
         const bool low_covered = tmin <= wi.omega0;
-        const bool top_ok = ((int)need.size() >= wi.k) || (tmax >= wi.omega0 + wi.delta);
+        const bool top_ok = (nsel_need >= wi.k) || (tmax >= wi.omega0 + wi.delta);
         if (!low_covered) {
           ok = false;  // targets do not reach down to omega0: move the centre down
           wi.shift = std::max(wi.omega0, wi.shift - 0.5 * (tmin - wi.omega0) - 0.25 * (tmax - tmin));
@@ -1288,6 +1336,7 @@ struct WindowBatch {
     wi.m = kept;
     wi.adjust = 0;
     wi.stall = 0;
+    wi.guard_wait = 0;
     wi.best_worst = 1e300;
   }
 
@@ -1459,6 +1508,9 @@ void window_batch_step(WindowBatch *wb) { wb->step(); }
 bool window_batch_finished(const WindowBatch *wb, int slot) { return wb->finished(slot); }
 WindowResult window_batch_take(WindowBatch *wb, int slot) { return wb->take(slot); }
 int window_batch_capacity(const WindowBatch *wb) { return wb->cap; }
+size_t window_batch_bytes(const WindowBatch *wb) {
+  return wb->mem.bytes + wb->D.bytes + wb->MD.bytes + wb->SD.bytes + wb->part.bytes + wb->small.bytes;
+}
 int window_batch_used(const WindowBatch *wb) { return wb->used(); }
 
 pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta,

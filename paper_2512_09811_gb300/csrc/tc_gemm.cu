@@ -573,6 +573,20 @@ struct TcPlan {
   DevBuf err;
 };
 
+size_t tc_plan_bytes(const pp_ctx *c) {
+  if (!c->tc) return 0;
+  TcPlan *p = c->tc;
+  const DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->bvv_hi, &p->bvv_lo, &p->bov_hi, &p->bov_lo, &p->gam_hi,
+                          &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_gap, &p->f_eps,
+                          &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
+                          &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
+                          &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
+                          &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err};
+  size_t n = 0;
+  for (const DevBuf *b : bufs) n += b->bytes;
+  return n;
+}
+
 void tc_destroy(pp_ctx *c) {
   if (!c->tc) return;
   TcPlan *p = c->tc;

@@ -1,7 +1,8 @@
 """Window roots of the FP64 form and of the mixed-precision form against the dense oracle.
 
 Dot 32/128/384 (ph dimension 4096, perturbative width): the dense oracle (M has 8192^2
-entries) still finishes in about a minute on the host.  Bars: FP64 form 1e-8 Ha, mixed form
+entries) still finishes in about a minute on the host.  Four windows (k = 4 and 8, widths
+0.05-0.1 Ha) at different depths of the spectrum, solved one by one and all in one call.  Bars: FP64 form 1e-8 Ha, mixed form
 (BF16 tensor-core sigma, FP64 Krylov, split-BF16 refinement) 1e-6 Ha.  Oscillator strengths:
 1e-4 relative in the FP64 form for roots whose neighbours are at least 1e-5 Ha away.  In the
 mixed form the returned vector is an eigenvector of the reduced-precision operator; it mixes
@@ -22,18 +23,22 @@ pytestmark = pytest.mark.gpu
 O, V, Q, SEED = 32, 128, 384, 3
 
 
+WINDOWS = [(20, 0.1, 8), (15, 0.08, 4), (40, 0.06, 4), (30, 0.05, 8)]  # (percentile, width, k)
+
+
 @pytest.fixture(scope="module")
 def case():
     inp = make_inputs(O, V, Q, seed=SEED, mode="perturbative")
     S, A, Bm = po.dense_blocks(inp.eps, inp.B, O, 2)
     ref = po.solve_dense(S, A, Bm, inp.mu)
     dA, dS = po.SigmaRef(inp.eps, inp.B, O, order=2).diag()
-    w0 = float(np.percentile((dA / dS).ravel(), 20))
-    return inp, ref, w0
+    r = (dA / dS).ravel()
+    wins = [(float(np.percentile(r, p)), w, k) for (p, w, k) in WINDOWS]
+    return inp, ref, wins
 
 
-def _check(got, ref, w0, tol, mixed=False):
-    idx = po.select_window(ref["omega"], w0, 0.1, 8, select=0)
+def _check(got, ref, w0, width, k, tol, mixed=False):
+    idx = po.select_window(ref["omega"], w0, width, k, select=0)
     assert len(got["omega"]) == len(idx)
     np.testing.assert_allclose(got["omega"], ref["omega"][idx], atol=tol, rtol=0)
     allw = ref["omega"]
@@ -53,23 +58,32 @@ def _check(got, ref, w0, tol, mixed=False):
 
 
 def test_fp64_form_matches_dense(cuda_lib, case):
+    """All windows in one pp_solve_windows call (their directions share each sigma batch)."""
     pp = cuda_lib
-    inp, ref, w0 = case
+    inp, ref, wins = case
     dot = pp.Dot(inp, prec=pp.PP_FP64, order=2, select=0, res_tol=1e-8, max_iter=300)
     try:
-        got = dot.solve_window(w0, 0.1, 8)
+        outs, st = dot.solve_windows([w[0] for w in wins], [w[1] for w in wins], [w[2] for w in wins])
     finally:
         dot.close()
-    _check(got, ref, w0, 1e-8)
+    assert st == pp.PP_OK
+    for (w0, width, k), got in zip(wins, outs):
+        _check(got, ref, w0, width, k, 1e-8)
 
 
 def test_mixed_form_matches_dense(cuda_lib, case):
+    """Each window alone, then all windows in one call: the same roots either way."""
     pp = cuda_lib
-    inp, ref, w0 = case
+    inp, ref, wins = case
     dot = pp.Dot(inp, prec=pp.PP_BF16, order=2, select=0, res_tol=1e-6, max_iter=300)
     try:
-        got = dot.solve_window(w0, 0.1, 8)
+        for (w0, width, k) in wins:
+            got = dot.solve_window(w0, width, k)
+            assert np.all(got["resid"] <= 1e-6)
+            _check(got, ref, w0, width, k, 1e-6, mixed=True)
+        outs, st = dot.solve_windows([w[0] for w in wins], [w[1] for w in wins], [w[2] for w in wins])
     finally:
         dot.close()
-    assert np.all(got["resid"] <= 1e-6)
-    _check(got, ref, w0, 1e-6, mixed=True)
+    assert st == pp.PP_OK
+    for (w0, width, k), got in zip(wins, outs):
+        _check(got, ref, w0, width, k, 1e-6, mixed=True)
