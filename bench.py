@@ -237,13 +237,18 @@ def run_ours(args, world, rank, local):
     sig_tflops = sigma_flops(w["nocc"], w["nvir"], w["naux"], 8) / (sig_ms / 1e3) / 1e12
 
     # end to end through the C ABI from host buffers: create (B to the device), solve, results back
+    from synth.inputs import DotInputs
+
+    # the host inputs in pinned memory
+    pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(inp, f))).pin_memory().numpy() for f in ("eps", "B", "mu")}
+    pinned = DotInputs(nocc=inp.nocc, nvir=inp.nvir, naux=inp.naux, sigma_b=inp.sigma_b, seed=inp.seed, **pin)
     h2d = inp.eps.nbytes + inp.B.nbytes + inp.mu.nbytes
     d2h = w["k"] * 3 * 8
     torch.cuda.synchronize()
     t0 = time.time()
     ee = 0
     for _ in range(max(1, min(args.steps, 2))):
-        d2 = pp.Dot(inp, **opt_kw)
+        d2 = pp.Dot(pinned, **opt_kw)
         o2 = d2.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
         ee += int(np.count_nonzero(o2["resid"] <= RES_TOL * 1.0000001))
         d2.close()
@@ -280,6 +285,67 @@ def run_ours(args, world, rank, local):
     )
     dot.close()
     return line
+
+
+SERVING_SIZES = [(32, 128, 384), (64, 256, 768), (128, 512, 1536)]
+
+
+def serving_leg(args):
+    """Poisson arrivals of window requests over a pool of dots (4 per size), served by the
+    continuous-batching loop; latency = finish - submit as the server records it."""
+    import paper_2512_09811_gb300 as pp
+    from synth.inputs import make_inputs
+
+    rng = np.random.default_rng(3)
+    sizes = SERVING_SIZES if args.serving_all_sizes else SERVING_SIZES[:2]
+    n_req, rate = args.serving_requests, args.serving_rate
+    opts = dict(prec=pp.PP_BF16, order=2, select=0, res_tol=RES_TOL, max_iter=300)
+    pool = []  # (size index, inputs, sorted diag(A)/diag(S))
+    for si, (o, v, Q) in enumerate(sizes):
+        for di in range(4):
+            inp = make_inputs(o, v, Q, seed=3000 + 10 * si + di, mode="perturbative")
+            d = pp.Dot(inp, **opts)
+            dA, dS = d.diagonal()
+            d.close()
+            pool.append((si, inp, np.sort((dA / dS).ravel())))
+    reqs = []
+    t = 0.0
+    for _ in range(n_req):
+        t += rng.exponential(1.0 / rate)
+        si = int(rng.integers(len(sizes)))
+        di = int(rng.integers(4))
+        k = int(rng.choice([4, 8, 16]))
+        width = float(rng.uniform(0.05, 0.2))
+        r = pool[4 * si + di][2]
+        w0 = float(rng.uniform(np.percentile(r, 10), np.percentile(r, 50)))
+        reqs.append((t, 4 * si + di, w0, width, k))
+    srv = pp.Server(200 << 30, slots_per_dot=4, nworkers=4, **opts)
+    try:
+        ids = [srv.add_dot(p_[1]) for p_ in pool]
+        t0 = time.perf_counter()
+        rid = []
+        for (ta, dot, w0, width, k) in reqs:
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            rid.append((srv.submit(ids[dot], w0, width, k), k, ta))
+        lat, roots, finish, notconv = [], 0, 0.0, 0
+        for (r_id, k, ta) in rid:
+            out = srv.wait(r_id, k, timeout_ms=1_800_000, allow_notconv=True)
+            lat.append(out["latency_ms"])
+            roots += int(np.count_nonzero(out["resid"] <= RES_TOL * 1.0000001))
+            notconv += int(out["status"] != pp.PP_OK)
+            finish = max(finish, ta + out["latency_ms"] / 1e3)
+        st = srv.stats()
+    finally:
+        srv.close()
+    return dict(requests=n_req, arrival_rate_per_s=rate, sizes=[list(z) for z in sizes], dots_per_size=4,
+                k_choices=[4, 8, 16], window_ha=[0.05, 0.2], start="U[pct10, pct50] of diag(A)/diag(S)",
+                p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                roots_per_s=roots / finish, roots=roots, wall_s=finish, not_converged=notconv,
+                slots_per_dot=4, workers=4, max_concurrent_dots=st["max_concurrent_dots"],
+                max_windows_per_step=st["max_windows_per_step"], ctx_created=st["ctx_created"],
+                ctx_evicted=st["ctx_evicted"], failed=st["failed"])
 
 
 def run_reference(args, world, rank):
@@ -374,6 +440,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace leg")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-rate", type=float, default=50.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serving-all-sizes", action="store_true",
+                    help="include 128/512/1536 dots in the serving mix (minutes per request)")
     ap.add_argument("--profile-sigma", action="store_true",
                     help="profiling workload: create the dot, two BF16 sigma batches of 8 supervectors")
     ap.add_argument("--profile-solve", type=int, default=0,
@@ -390,6 +461,8 @@ def main():
         return
     line = run_ours(args, world, rank, local)
     if rank == 0:
+        if world == 1 and not args.no_serving:
+            line["serving"] = serving_leg(args)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         print(json.dumps(line), flush=True)

@@ -85,6 +85,9 @@ typedef struct {
   int refine;          /* PP_BF16 only: split-precision refinement steps (default on) */
   uint64_t seed;       /* reserved for random initial vectors */
   void *cuda_stream;   /* cudaStream_t to use, or NULL to create one */
+  double workspace_gb; /* device memory for one chunk of the tensor-core sigma workspaces
+                          (0 = automatic: a quarter of the free memory at first use, between
+                          12 and 64 GB) */
 } pp_options;
 
 /* Fill *opt with the defaults above. */
@@ -153,8 +156,10 @@ pp_status pp_diagonal(pp_ctx *ctx, double *diagA, double *diagS);
 /*
  * Roots of Eq. (m_eigen) inside one window (Sec. 2.5: weighted-Jacobi inverse
  * Krylov basis, folded-spectrum Rayleigh-Ritz on (M - omega Sigma)^2).
- *   select 0 (options): the k lowest roots in [omega0, omega0 + delta];
- *   select 1:           the k roots nearest omega0 (delta ignored).
+ *   select 0 (options): the k lowest roots in [omega0, omega0 + delta]; more than 8 are
+ *                       found 8 at a time, each group starting 2 res_tol above the last root
+ *                       of the previous one (roots closer than that are reported once);
+ *   select 1:           the k roots nearest omega0 (delta ignored), k <= 24.
  *   omega[k], osc[k], resid[k]: host outputs, ascending omega; osc is 0 if mu was NULL.
  *   vecs: NULL or host [k][2][nocc][nvir], normalised X^T S X - Y^T S Y = 1.
  *   *nfound: number of roots written (< k if the window holds fewer).
@@ -229,7 +234,8 @@ typedef struct {
 /*
  * hbm_budget: device bytes the resident dots may hold (an estimate per dot until it has
  * run, then its measured allocations).  opt: solver options for every dot (opt->cuda_stream
- * must be NULL: each dot gets its own stream; NULL = defaults).  slots_per_dot: windows a
+ * must be NULL: each dot gets its own stream; NULL = defaults; workspace_gb 0 means 12 GB
+ * per dot here).  slots_per_dot: windows a
  * dot advances together (1..16).  nworkers: worker threads (0 = 4, at most 16).  The
  * current device is the server's device.
  */

@@ -95,7 +95,8 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
   if (opt) o = *opt;
   else pp_default_options(&o);
   if (o.order < 0 || o.order > 2 || (o.prec != PP_FP64 && o.prec != PP_BF16 && o.prec != PP_BF16X3) || o.block < 1 ||
-      o.m_max < 4 || !(o.res_tol > 0) || !(o.jacobi_floor > 0) || (o.select != 0 && o.select != 1)) {
+      o.m_max < 4 || !(o.res_tol > 0) || !(o.jacobi_floor > 0) || (o.select != 0 && o.select != 1) ||
+      !(o.workspace_gb >= 0) || o.workspace_gb > 1e5) {
     g_create_err = "pp_create: bad options";
     return PP_EINVAL;
   }

@@ -181,6 +181,7 @@ int window_batch_capacity(const WindowBatch *wb);
 size_t window_batch_bytes(const WindowBatch *wb);
 // device bytes held by the tensor-core plan (tc_gemm.cu) and by a whole context (capi.cu)
 size_t tc_plan_bytes(const pp_ctx *c);
+long long tc_workspace_bytes(const pp_ctx *c);
 size_t ctx_device_bytes(const pp_ctx *c);
 int window_batch_used(const WindowBatch *wb);
 // dispatch of one sigma application (solver and C ABI)

@@ -72,7 +72,8 @@ size_t estimate_bytes(long long o, long long v, long long Q, const pp_options &o
     total += 4 * (ov + n + Q * ov + 2 * Q * o * o + 2 * Q * v * v + 3 * Q * ov + 2 * o * o + 2 * v * v);
     total += 4 * (ov * ldq + Q * v * vp + 2 * Q * o * vp + v * v * Qp + o * o * Qp);
     const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 4 * Q * ldT + 8 * ov * Qp;
-    long long R = std::max<long long>(2, std::min<long long>((12LL << 30) / std::max<long long>(per_half, 1), 64));
+    const long long ws = (long long)(opt.workspace_gb * (1LL << 30));
+    long long R = std::max<long long>(2, std::min<long long>(ws / std::max<long long>(per_half, 1), 64));
     R = std::min(R & ~1LL, rows_max);
     total += per_half * R + 4 * (64LL << 20);
   } else {
@@ -311,6 +312,7 @@ extern "C" pp_status pp_server_create(size_t hbm_budget, const pp_options *opt, 
   if (opt) o = *opt;
   else pp_default_options(&o);
   if (o.cuda_stream) return PP_EINVAL;  // every dot gets its own stream
+  if (!(o.workspace_gb > 0)) o.workspace_gb = 12.0;  // a fixed share per dot: the budget is per dot
   pp_server *S = new (std::nothrow) pp_server();
   if (!S) return PP_ENOMEM;
   S->budget = hbm_budget;

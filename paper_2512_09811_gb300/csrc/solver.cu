@@ -837,8 +837,23 @@ struct Window {
   double best_worst = 1e300;  // BF16 phase: best worst-residual seen, and iterations without gain
   int stall = 0;
   int guard_wait = 0;  // iterations spent waiting for guard targets only
-  WindowResult res;
+  // select 0 with k > KCHUNK: the roots are found KCHUNK at a time, each chunk restarting just
+  // above the last root found; k_total and omega_end describe the whole request
+  int k_total = 0;
+  double omega_end = 0;
+  int iter0 = 0;     // iterations before the current chunk (max_iter applies per chunk)
+  WindowResult res;  // accumulated results
 };
+
+// A single block of more than KCHUNK targets fills up with spurious interior Ritz values
+// (mixtures of roots far apart, residuals of order 0.1) and stalls; larger requests are
+// solved as consecutive chunks of KCHUNK roots.
+constexpr int KCHUNK = 8;
+// Ritz pairs with a residual above this are uninformative (the root they stand for could be
+// anywhere within that distance, and spurious interior values sit there for good); they are
+// neither reported nor counted among the roots a window needs.  Genuine approximations are
+// below 2e-2 from the first iteration on.
+constexpr double kSpurRes = 3e-2;
 
 }  // namespace
 
@@ -952,7 +967,7 @@ struct WindowBatch {
   // A new window in a free slot (-1 if none).  Its initial block is formed by the next step.
   int add(double omega0, double delta, int k) {
     if (k <= 0) throw PPError(PP_EINVAL, "k must be positive");
-    if (k > 24) throw PPError(PP_EINVAL, "k must be at most 24 per window");
+    if (c->opt.select == 1 && k > 24) throw PPError(PP_EINVAL, "k must be at most 24 for select = 1");
     int slot = -1;
     for (int w = 0; w < cap; ++w)
       if (!W[w].used) {
@@ -966,9 +981,20 @@ struct WindowBatch {
     wi.finished = false;
     wi.omega0 = omega0;
     wi.delta = delta;
-    wi.k = k;
-    wi.m = 0;
+    wi.k_total = k;
+    wi.omega_end = omega0 + delta;
+    wi.k = (c->opt.select == 0) ? std::min(k, KCHUNK) : k;
     wi.iters = 0;
+    wi.res = WindowResult();
+    start_chunk(wi);
+    return slot;
+  }
+
+  // fresh state, targets and block size for the current chunk: k roots from omega0 up
+  void start_chunk(Window &wi) {
+    wi.fresh = true;
+    wi.iter0 = wi.iters;
+    wi.m = 0;
     wi.adjust = 0;
     wi.stall = 0;
     wi.guard_wait = 0;
@@ -977,7 +1003,6 @@ struct WindowBatch {
     wi.ndir = wi.nnew = 0;
     wi.prec = prec0;
     wi.tol = refine ? std::max(c->opt.res_tol, 1e-5) : c->opt.res_tol;
-    wi.res = WindowResult();
     if (c->opt.select == 1) {
       wi.shift = wi.omega0;
       wi.nev = wi.k + 2;
@@ -995,7 +1020,6 @@ struct WindowBatch {
     wi.b = std::min(bcap, std::max(wi.nev + 2, c->opt.block));
     wi.b = std::min<int>(wi.b, (int)L);
     wi.nev = std::min(wi.nev, wi.b);
-    return slot;
   }
 
   bool finished(int slot) const { return W[slot].used && W[slot].finished; }
@@ -1023,13 +1047,15 @@ struct WindowBatch {
 
   // results of a window from its last extraction (the selection rules of pp_solve_window)
   void finalize(Window &wi, int status) {
-    WindowResult &r = wi.res;
+    WindowResult r;  // this chunk
     r.status = status;
     r.iters = wi.iters;
     const int nb = (int)wi.order.size();
     std::vector<int> sel;
     if (c->opt.select == 1) {
-      std::vector<int> cand(wi.order.begin(), wi.order.end());
+      std::vector<int> cand;
+      for (int j : wi.order)
+        if (wi.h_res[j] <= kSpurRes) cand.push_back(j);
       std::stable_sort(cand.begin(), cand.end(), [&](int a, int b2) {
         double da = fabs(wi.h_theta[a] - wi.omega0), db = fabs(wi.h_theta[b2] - wi.omega0);
         return da < db || (da == db && wi.h_theta[a] < wi.h_theta[b2]);
@@ -1039,7 +1065,8 @@ struct WindowBatch {
       std::vector<int> in;
       for (int t = 0; t < nb; ++t) {
         int j = wi.order[t];
-        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
+        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta && wi.h_res[j] <= kSpurRes)
+          in.push_back(j);
       }
       std::stable_sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
       for (int j = 0; j < (int)in.size() && (int)sel.size() < wi.k; ++j) sel.push_back(in[j]);
@@ -1081,6 +1108,26 @@ struct WindowBatch {
           double *vv = r.vecs.data() + (size_t)t * L;
           for (long long l = 0; l < L; ++l) vv[l] *= sc;
         }
+    }
+    // append this chunk; a full chunk of a larger request restarts above its last root (the
+    // offset 2 res_tol keeps a root found again within its tolerance out of the next chunk)
+    WindowResult &acc = wi.res;
+    acc.status = status;
+    acc.iters = wi.iters;
+    acc.omega.insert(acc.omega.end(), r.omega.begin(), r.omega.end());
+    acc.osc.insert(acc.osc.end(), r.osc.begin(), r.osc.end());
+    acc.resid.insert(acc.resid.end(), r.resid.begin(), r.resid.end());
+    acc.vecs.insert(acc.vecs.end(), r.vecs.begin(), r.vecs.end());
+    const int got = (int)acc.omega.size();
+    if (c->opt.select == 0 && status == PP_OK && nf == wi.k && got < wi.k_total) {
+      const double start = acc.omega.back() + std::max(1e-9, 2.0 * c->opt.res_tol);
+      if (start < wi.omega_end) {
+        wi.omega0 = start;
+        wi.delta = wi.omega_end - start;
+        wi.k = std::min(KCHUNK, wi.k_total - got);
+        start_chunk(wi);
+        return;
+      }
     }
     wi.finished = true;
   }
@@ -1180,11 +1227,13 @@ struct WindowBatch {
     // (select 0) or the k targets nearest omega0 (select 1); only they must meet the tolerance
     std::vector<int> need;
     if (c->opt.select == 1) {
-      for (int t = 0; t < b && (int)need.size() < wi.k; ++t) need.push_back(wi.order[t]);
+      for (int t = 0; t < b && (int)need.size() < wi.k; ++t)
+        if (wi.h_res[wi.order[t]] <= kSpurRes) need.push_back(wi.order[t]);
     } else {
       std::vector<int> in;
       for (int j = 0; j < b; ++j)
-        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta) in.push_back(j);
+        if (wi.h_theta[j] >= wi.omega0 && wi.h_theta[j] <= wi.omega0 + wi.delta && wi.h_res[j] <= kSpurRes)
+          in.push_back(j);
       std::sort(in.begin(), in.end(), [&](int a, int b2) { return wi.h_theta[a] < wi.h_theta[b2]; });
       for (int j = 0; j < (int)in.size() && (int)need.size() < wi.k; ++j) need.push_back(in[j]);
     }
@@ -1292,7 +1341,7 @@ struct WindowBatch {
         return 0;
       }
     }
-    if (wi.iters >= std::max(1, c->opt.max_iter)) {
+    if (wi.iters - wi.iter0 >= std::max(1, c->opt.max_iter)) {
       finalize(wi, PP_ENOTCONV);
       return 0;
     }

@@ -648,6 +648,14 @@ static void bf16_pair(DevBuf &hi, DevBuf &lo, const double *src, long long rows,
 
 static long long pad64(long long x) { return std::max<long long>(tc::BK, ((x + tc::BK - 1) / tc::BK) * tc::BK); }
 
+// device bytes for one chunk of the tensor-core sigma workspaces
+long long tc_workspace_bytes(const pp_ctx *c) {
+  if (c->opt.workspace_gb > 0) return (long long)(c->opt.workspace_gb * (1LL << 30));
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 12LL << 30;
+  return std::min<long long>(64LL << 30, std::max<long long>(12LL << 30, (long long)(free_b / 4)));
+}
+
 // Stage 1 of the plan: everything that depends on B and eps only (the precompute needs it).
 static TcPlan *tc_plan_operands(pp_ctx *c) {
   if (c->tc) return c->tc;
@@ -693,7 +701,7 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   // chunk of R half-vectors: FP32 W, U, E/F plus BF16 C_Q(V) and two BF16 copies of P
   const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 2 * 2 * Q * p->ldT +
                              2 * 2 * 2 * ov * p->Qp;
-  long long R = (12LL << 30) / std::max<long long>(per_half, 1);
+  long long R = tc_workspace_bytes(c) / std::max<long long>(per_half, 1);
   R = std::max<long long>(2, std::min<long long>(R, 64));
   R &= ~1LL;
   p->Rmax = (int)R;

@@ -96,8 +96,7 @@ def test_serving_rejects_bad_requests(cuda_lib):
             srv.submit(did + 5, 1.0, 0.1, 4)
         with pytest.raises(pp.PPError):
             srv.submit(did, 1.0, 0.1, 0)
-        rid = srv.submit(did, 0.5, 0.5, 40)  # k above the per-window limit: fails cleanly
         with pytest.raises(pp.PPError):
-            srv.wait(rid, 40, timeout_ms=120_000)
+            srv.submit(did, 1.0, -0.1, 4)  # negative width
     finally:
         srv.close()
