@@ -580,21 +580,27 @@ __device__ double blk_sum(double x, double *red) {
   return r;
 }
 
-// Folded-spectrum vectors with deflation (one CTA, 256 threads).  For target j:
+// Folded-spectrum vectors with deflation, one warp (the reduced problem has m <= 32, so every
+// loop below is at most a few passes per lane and no block-wide barrier is needed).  For
+// target j:
 //   w <- th0[j]; repeat reps times:
 //     G(w) = (MV - w SV)^T (MV - w SV) = Gmm - w (Gms + Gms^T) + w^2 Gss,
 //     restricted to coefficients Euclidean-orthogonal to Hs c_i (i < j) by a penalty,
 //     c <- smallest eigenvector (inverse iteration from the previous c), w <- c^T Hm c / c^T Hs c.
-__global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
-                                                 const double *__restrict__ Hs,
-                                                 const double *__restrict__ Gmm,
-                                                 const double *__restrict__ Gms,
-                                                 const double *__restrict__ Gss, int m, int b,
-                                                 int reps, const double *__restrict__ th0,
-                                                 const double *__restrict__ C0,
-                                                 double *__restrict__ Cout,
-                                                 double *__restrict__ thout,
-                                                 int *__restrict__ status) {
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
+                                                const double *__restrict__ Hs,
+                                                const double *__restrict__ Gmm,
+                                                const double *__restrict__ Gms,
+                                                const double *__restrict__ Gss, int m, int b,
+                                                int reps, const double *__restrict__ th0,
+                                                const double *__restrict__ C0,
+                                                double *__restrict__ Cout,
+                                                double *__restrict__ thout,
+                                                int *__restrict__ status) {
   extern __shared__ double sm[];
   const int ld = m + 1;
   double *G = sm;               // m x ld
@@ -603,52 +609,51 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
   double *c = GQ + m * b;       // m
   double *t1 = c + m;           // m
   double *dL = t1 + m;          // m
-  __shared__ double red[256];
   __shared__ double qgq[32 * 32];
   __shared__ double Zs[32 * 32];
-  __shared__ int ok_s;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = threadIdx.x;
   for (int j = 0; j < b; ++j) {
     double w = th0[j];
-    for (int i = tid; i < m; i += nt) c[i] = C0[(long long)j * m + i];
-    __syncthreads();
-    for (int rep = 0; rep < reps; ++rep) {
+    for (int i = lane; i < m; i += 32) c[i] = C0[(long long)j * m + i];
+    __syncwarp();
+    bool ok = true;
+    for (int rep = 0; rep < reps && ok; ++rep) {
       double tr = 0.0;
-      for (int idx = tid; idx < m * m; idx += nt) {
+      for (int idx = lane; idx < m * m; idx += 32) {
         int i = idx / m, k = idx % m;
         double g = 0.5 * (Gmm[i * m + k] + Gmm[k * m + i]) - w * (Gms[i * m + k] + Gms[k * m + i]) +
                    w * w * 0.5 * (Gss[i * m + k] + Gss[k * m + i]);
         G[i * ld + k] = g;
         if (i == k) tr += g;
       }
-      tr = blk_sum(tr, red);
+      tr = warp_sum(tr);
       const double gamma = 10.0 * tr + 1e-300, delta = 1e-14 * tr + 1e-300;
+      __syncwarp();
       if (j > 0) {
-        // GQ = G Q^T (m x j); qgq = Q G Q^T (j x j)
-        for (int idx = tid; idx < m * j; idx += nt) {
+        // GQ = G Q^T (m x j); qgq = Q G Q^T (j x j); Z = Q^T qgq (m x j)
+        for (int idx = lane; idx < m * j; idx += 32) {
           int i = idx / j, p = idx % j;
-          double s = 0.0;
-          for (int k = 0; k < m; ++k) s += G[i * ld + k] * Qc[p * m + k];
-          GQ[i * b + p] = s;
+          double sacc = 0.0;
+          for (int k = 0; k < m; ++k) sacc += G[i * ld + k] * Qc[p * m + k];
+          GQ[i * b + p] = sacc;
         }
-        __syncthreads();
-        for (int idx = tid; idx < j * j; idx += nt) {
+        __syncwarp();
+        for (int idx = lane; idx < j * j; idx += 32) {
           int p = idx / j, q = idx % j;
-          double s = 0.0;
-          for (int i = 0; i < m; ++i) s += Qc[p * m + i] * GQ[i * b + q];
-          qgq[p * 32 + q] = s;
+          double sacc = 0.0;
+          for (int i = 0; i < m; ++i) sacc += Qc[p * m + i] * GQ[i * b + q];
+          qgq[p * 32 + q] = sacc;
         }
-        __syncthreads();
-        // Z[i][p] = sum_q Q_q[i] qgq[q][p]  (so Q qgq Q^T = Z Q)
-        for (int idx = tid; idx < m * j; idx += nt) {
+        __syncwarp();
+        for (int idx = lane; idx < m * j; idx += 32) {
           int i = idx / j, p = idx % j;
           double z = 0.0;
           for (int q = 0; q < j; ++q) z += Qc[q * m + i] * qgq[q * 32 + p];
           Zs[i * 32 + p] = z;
         }
-        __syncthreads();
+        __syncwarp();
         // G <- (1 - QQ^T) G (1 - QQ^T) + gamma QQ^T
-        for (int idx = tid; idx < m * m; idx += nt) {
+        for (int idx = lane; idx < m * m; idx += 32) {
           int i = idx / m, k = idx % m;
           double g = G[i * ld + k];
           for (int p = 0; p < j; ++p) {
@@ -657,41 +662,44 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
           }
           G[i * ld + k] = g;
         }
-        __syncthreads();
+        __syncwarp();
       }
-      for (int i = tid; i < m; i += nt) G[i * ld + i] += delta;
-      __syncthreads();
-      if (tid < 32) {
-        bool ok = warp_cholesky(G, ld, m, dL);
-        if (tid == 0) ok_s = ok ? 1 : 0;
-      }
-      __syncthreads();
-      if (!ok_s) {
-        if (tid == 0) *status = 2;
+      for (int i = lane; i < m; i += 32) G[i * ld + i] += delta;
+      __syncwarp();
+      ok = warp_cholesky(G, ld, m, dL);
+      if (!ok) {
+        if (lane == 0) *status = 2;
         break;
       }
       for (int itv = 0; itv < 4; ++itv) {
-        // project c off the constraint directions and normalise
+        // project c off the constraint directions (all at once: Q is orthonormal) and normalise
         for (int p = 0; p < j; ++p) {
-          double s = 0.0;
-          for (int i = tid; i < m; i += nt) s += Qc[p * m + i] * c[i];
-          s = blk_sum(s, red);
-          for (int i = tid; i < m; i += nt) c[i] -= s * Qc[p * m + i];
-          __syncthreads();
+          double sp = 0.0;
+          for (int i = lane; i < m; i += 32) sp += Qc[p * m + i] * c[i];
+          sp = warp_sum(sp);
+          if (lane == 0) t1[p] = sp;
         }
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) {
+          double ci = c[i];
+          for (int p = 0; p < j; ++p) ci -= t1[p] * Qc[p * m + i];
+          c[i] = ci;
+        }
+        __syncwarp();
         double nn = 0.0;
-        for (int i = tid; i < m; i += nt) nn += c[i] * c[i];
-        nn = blk_sum(nn, red);
+        for (int i = lane; i < m; i += 32) nn += c[i] * c[i];
+        nn = warp_sum(nn);
         if (!(nn > 0.0)) nn = 1.0;
-        for (int i = tid; i < m; i += nt) c[i] /= sqrt(nn);
-        __syncthreads();
+        const double inv = 1.0 / sqrt(nn);
+        for (int i = lane; i < m; i += 32) c[i] *= inv;
+        __syncwarp();
         if (itv == 3) break;
-        if (tid < 32) warp_chol_solve(G, ld, m, dL, c);
-        __syncthreads();
+        warp_chol_solve(G, ld, m, dL, c);
+        __syncwarp();
       }
       // fold centre follows the Rayleigh quotient of the folded vector
       double nm = 0.0, ns = 0.0;
-      for (int i = tid; i < m; i += nt) {
+      for (int i = lane; i < m; i += 32) {
         double hm = 0.0, hs = 0.0;
         for (int k = 0; k < m; ++k) {
           hm += Hm[i * m + k] * c[k];
@@ -700,33 +708,33 @@ __global__ void __launch_bounds__(256) k_refined(const double *__restrict__ Hm,
         nm += c[i] * hm;
         ns += c[i] * hs;
       }
-      nm = blk_sum(nm, red);
-      ns = blk_sum(ns, red);
+      nm = warp_sum(nm);
+      ns = warp_sum(ns);
       if (fabs(ns) > 1e-300) w = nm / ns;
     }
-    for (int i = tid; i < m; i += nt) Cout[(long long)j * m + i] = c[i];
-    if (tid == 0) thout[j] = w;
+    for (int i = lane; i < m; i += 32) Cout[(long long)j * m + i] = c[i];
+    if (lane == 0) thout[j] = w;
     // new constraint direction: Hs c, orthonormalised against the previous ones (twice)
-    for (int i = tid; i < m; i += nt) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += Hs[i * m + k] * c[k];
-      t1[i] = s;
+    for (int i = lane; i < m; i += 32) {
+      double sacc = 0.0;
+      for (int k = 0; k < m; ++k) sacc += Hs[i * m + k] * c[k];
+      t1[i] = sacc;
     }
-    __syncthreads();
+    __syncwarp();
     for (int pass = 0; pass < 2; ++pass)
       for (int p = 0; p < j; ++p) {
-        double s = 0.0;
-        for (int i = tid; i < m; i += nt) s += Qc[p * m + i] * t1[i];
-        s = blk_sum(s, red);
-        for (int i = tid; i < m; i += nt) t1[i] -= s * Qc[p * m + i];
-        __syncthreads();
+        double sp = 0.0;
+        for (int i = lane; i < m; i += 32) sp += Qc[p * m + i] * t1[i];
+        sp = warp_sum(sp);
+        for (int i = lane; i < m; i += 32) t1[i] -= sp * Qc[p * m + i];
+        __syncwarp();
       }
     double nn = 0.0;
-    for (int i = tid; i < m; i += nt) nn += t1[i] * t1[i];
-    nn = blk_sum(nn, red);
+    for (int i = lane; i < m; i += 32) nn += t1[i] * t1[i];
+    nn = warp_sum(nn);
     double inv = (nn > 1e-300) ? 1.0 / sqrt(nn) : 0.0;
-    for (int i = tid; i < m; i += nt) Qc[j * m + i] = t1[i] * inv;
-    __syncthreads();
+    for (int i = lane; i < m; i += 32) Qc[j * m + i] = t1[i] * inv;
+    __syncwarp();
   }
 }
 
@@ -1172,7 +1180,7 @@ struct WindowBatch {
       g.C = wi.C0; g.c_m = nr; g.c_n = 1;
       gemm_f64(g, s);
     }
-    k_refined<<<1, 256, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
+    k_refined<<<1, 32, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
         wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
     PP_LAUNCH_CHECK("k_refined");
     sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);

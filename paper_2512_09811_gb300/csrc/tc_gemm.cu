@@ -227,10 +227,46 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const long long rbase = (row / o.d_r) * o.s_r1 + (row % o.d_r) * o.s_r0;
     const long long rbase2 = two ? (row / o2.d_r) * o2.s_r1 + (row % o2.d_r) * o2.s_r0 : 0;
+    // BF16-pair outputs whose columns run contiguously in groups of 8 (16-byte aligned) are
+    // written 8 values per store
+    auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    const bool vec8 = !o.C && al16(o.Chi) && al16(o.Clo) && (!two || (al16(o2.Chi) && al16(o2.Clo))) &&
+                      o.s_c0 == 1 && (o.d_c % 8) == 0 && (o.s_r0 % 8) == 0 && (o.s_r1 % 8) == 0 &&
+                      (o.s_c1 % 8) == 0 && (!two || (!o2.C && o2.s_c0 == 1 && (o2.d_c % 8) == 0 &&
+                                                    (o2.s_r0 % 8) == 0 && (o2.s_r1 % 8) == 0 && (o2.s_c1 % 8) == 0));
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + c0, v);
-      if (row < args.M) {
+      if (row < args.M && vec8) {
+        for (int g = 0; g < 4; ++g) {
+          const long long col = n0 + c0 + 8 * g;
+          if (col >= args.N) break;
+          if (col + 8 > args.N) {  // ragged tail: element by element
+            for (int q = 0; q < 8 && col + q < args.N; ++q) {
+              const long long cc = col + q;
+              epi_store(o, rbase + (cc / o.d_c) * o.s_c1 + (cc % o.d_c), o.alpha * v[8 * g + q]);
+              if (two) epi_store(o2, rbase2 + (cc / o2.d_c) * o2.s_c1 + (cc % o2.d_c), o2.alpha * v[8 * g + q]);
+            }
+            continue;
+          }
+          for (int t = 0; t < (two ? 2 : 1); ++t) {
+            const GemmOut &oo = t ? o2 : o;
+            const long long off = (t ? rbase2 : rbase) + (col / oo.d_c) * oo.s_c1 + (col % oo.d_c);
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float x0 = oo.alpha * v[8 * g + 2 * q], x1 = oo.alpha * v[8 * g + 2 * q + 1];
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+              const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+              const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+              hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            *reinterpret_cast<uint4 *>(oo.Chi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if (oo.Clo) *reinterpret_cast<uint4 *>(oo.Clo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+        }
+      } else if (row < args.M) {
         const long long col = n0 + c0;
         long long cb = col / o.d_c, cr = col % o.d_c;
         long long cb2 = two ? col / o2.d_c : 0, cr2 = two ? col % o2.d_c : 0;
