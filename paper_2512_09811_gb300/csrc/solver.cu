@@ -580,16 +580,37 @@ __device__ double blk_sum(double x, double *red) {
   return r;
 }
 
-// Folded-spectrum vectors with deflation, one warp (the reduced problem has m <= 32, so every
-// loop below is at most a few passes per lane and no block-wide barrier is needed).  For
+// Folded-spectrum vectors with deflation, one warp (the reduced problem has m <= 32).  For
 // target j:
 //   w <- th0[j]; repeat reps times:
 //     G(w) = (MV - w SV)^T (MV - w SV) = Gmm - w (Gms + Gms^T) + w^2 Gss,
-//     restricted to coefficients Euclidean-orthogonal to Hs c_i (i < j) by a penalty,
+//     restricted to coefficients Euclidean-orthogonal to Hs c_i (i < j): P G(w) P + gamma Q^T Q
+//     with P = 1 - Q^T Q, Q the orthonormal constraint directions,
 //     c <- smallest eigenvector (inverse iteration from the previous c), w <- c^T Hm c / c^T Hs c.
+// P G(w) P = Amm - w Ams + w^2 Ass with A = P G P for the three Grams; each new constraint
+// direction q (orthogonal to the earlier ones) updates them by a rank-2 term,
+//   A <- A - (A q) q^T - q (A q)^T + (q^T A q) q q^T,
+// so a repetition costs O(m^2) plus one Cholesky factorisation.
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
+}
+__device__ void warp_rank2_project(double *A, int ld, int m, const double *q, double *u) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < m; i += 32) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += A[i * ld + k] * q[k];
+    u[i] = s;
+  }
+  __syncwarp();
+  double a = 0.0;
+  for (int i = lane; i < m; i += 32) a += q[i] * u[i];
+  a = warp_sum(a);
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx / m, k = idx % m;
+    A[i * ld + k] += -u[i] * q[k] - q[i] * u[k] + a * q[i] * q[k];
+  }
+  __syncwarp();
 }
 __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
                                                 const double *__restrict__ Hs,
@@ -603,15 +624,24 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
                                                 int *__restrict__ status) {
   extern __shared__ double sm[];
   const int ld = m + 1;
-  double *G = sm;               // m x ld
-  double *Qc = G + m * ld;      // b x m, orthonormal constraint directions
-  double *GQ = Qc + b * m;      // m x b
-  double *c = GQ + m * b;       // m
+  double *Amm = sm;             // m x ld each: P Gmm P, P (Gms + Gms^T) P, P Gss P
+  double *Ams = Amm + m * ld;
+  double *Ass = Ams + m * ld;
+  double *QQ = Ass + m * ld;    // Q^T Q
+  double *F = QQ + m * ld;      // the shifted matrix, then its Cholesky factor
+  double *Qc = F + m * ld;      // b x m, orthonormal constraint directions
+  double *c = Qc + b * m;       // m
   double *t1 = c + m;           // m
   double *dL = t1 + m;          // m
-  __shared__ double qgq[32 * 32];
-  __shared__ double Zs[32 * 32];
   const int lane = threadIdx.x;
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx / m, k = idx % m;
+    Amm[i * ld + k] = 0.5 * (Gmm[i * m + k] + Gmm[k * m + i]);
+    Ams[i * ld + k] = Gms[i * m + k] + Gms[k * m + i];
+    Ass[i * ld + k] = 0.5 * (Gss[i * m + k] + Gss[k * m + i]);
+    QQ[i * ld + k] = 0.0;
+  }
+  __syncwarp();
   for (int j = 0; j < b; ++j) {
     double w = th0[j];
     for (int i = lane; i < m; i += 32) c[i] = C0[(long long)j * m + i];
@@ -619,60 +649,22 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
     bool ok = true;
     for (int rep = 0; rep < reps && ok; ++rep) {
       double tr = 0.0;
-      for (int idx = lane; idx < m * m; idx += 32) {
-        int i = idx / m, k = idx % m;
-        double g = 0.5 * (Gmm[i * m + k] + Gmm[k * m + i]) - w * (Gms[i * m + k] + Gms[k * m + i]) +
-                   w * w * 0.5 * (Gss[i * m + k] + Gss[k * m + i]);
-        G[i * ld + k] = g;
-        if (i == k) tr += g;
-      }
-      tr = warp_sum(tr);
+      for (int i = lane; i < m; i += 32) tr += Amm[i * ld + i] - w * Ams[i * ld + i] + w * w * Ass[i * ld + i];
+      tr = fabs(warp_sum(tr));
       const double gamma = 10.0 * tr + 1e-300, delta = 1e-14 * tr + 1e-300;
-      __syncwarp();
-      if (j > 0) {
-        // GQ = G Q^T (m x j); qgq = Q G Q^T (j x j); Z = Q^T qgq (m x j)
-        for (int idx = lane; idx < m * j; idx += 32) {
-          int i = idx / j, p = idx % j;
-          double sacc = 0.0;
-          for (int k = 0; k < m; ++k) sacc += G[i * ld + k] * Qc[p * m + k];
-          GQ[i * b + p] = sacc;
-        }
-        __syncwarp();
-        for (int idx = lane; idx < j * j; idx += 32) {
-          int p = idx / j, q = idx % j;
-          double sacc = 0.0;
-          for (int i = 0; i < m; ++i) sacc += Qc[p * m + i] * GQ[i * b + q];
-          qgq[p * 32 + q] = sacc;
-        }
-        __syncwarp();
-        for (int idx = lane; idx < m * j; idx += 32) {
-          int i = idx / j, p = idx % j;
-          double z = 0.0;
-          for (int q = 0; q < j; ++q) z += Qc[q * m + i] * qgq[q * 32 + p];
-          Zs[i * 32 + p] = z;
-        }
-        __syncwarp();
-        // G <- (1 - QQ^T) G (1 - QQ^T) + gamma QQ^T
-        for (int idx = lane; idx < m * m; idx += 32) {
-          int i = idx / m, k = idx % m;
-          double g = G[i * ld + k];
-          for (int p = 0; p < j; ++p) {
-            const double qi = Qc[p * m + i], qk = Qc[p * m + k];
-            g += (Zs[i * 32 + p] - GQ[i * b + p]) * qk - qi * GQ[k * b + p] + gamma * qi * qk;
-          }
-          G[i * ld + k] = g;
-        }
-        __syncwarp();
+      for (int idx = lane; idx < m * m; idx += 32) {
+        const int i = idx / m, k = idx % m;
+        F[i * ld + k] = Amm[i * ld + k] - w * Ams[i * ld + k] + w * w * Ass[i * ld + k] + gamma * QQ[i * ld + k] +
+                        (i == k ? delta : 0.0);
       }
-      for (int i = lane; i < m; i += 32) G[i * ld + i] += delta;
       __syncwarp();
-      ok = warp_cholesky(G, ld, m, dL);
+      ok = warp_cholesky(F, ld, m, dL);
       if (!ok) {
         if (lane == 0) *status = 2;
         break;
       }
       for (int itv = 0; itv < 4; ++itv) {
-        // project c off the constraint directions (all at once: Q is orthonormal) and normalise
+        // project c off the constraint directions (Q is orthonormal) and normalise
         for (int p = 0; p < j; ++p) {
           double sp = 0.0;
           for (int i = lane; i < m; i += 32) sp += Qc[p * m + i] * c[i];
@@ -694,7 +686,7 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
         for (int i = lane; i < m; i += 32) c[i] *= inv;
         __syncwarp();
         if (itv == 3) break;
-        warp_chol_solve(G, ld, m, dL, c);
+        warp_chol_solve(F, ld, m, dL, c);
         __syncwarp();
       }
       // fold centre follows the Rayleigh quotient of the folded vector
@@ -714,6 +706,7 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
     }
     for (int i = lane; i < m; i += 32) Cout[(long long)j * m + i] = c[i];
     if (lane == 0) thout[j] = w;
+    if (j + 1 == b) break;
     // new constraint direction: Hs c, orthonormalised against the previous ones (twice)
     for (int i = lane; i < m; i += 32) {
       double sacc = 0.0;
@@ -734,6 +727,16 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
     nn = warp_sum(nn);
     double inv = (nn > 1e-300) ? 1.0 / sqrt(nn) : 0.0;
     for (int i = lane; i < m; i += 32) Qc[j * m + i] = t1[i] * inv;
+    __syncwarp();
+    // fold it into the projected Grams and Q^T Q (the Cholesky buffer F is free as scratch)
+    const double *q = Qc + j * m;
+    warp_rank2_project(Amm, ld, m, q, F);
+    warp_rank2_project(Ams, ld, m, q, F);
+    warp_rank2_project(Ass, ld, m, q, F);
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int i = idx / m, k = idx % m;
+      QQ[i * ld + k] += q[i] * q[k];
+    }
     __syncwarp();
   }
 }
@@ -1180,7 +1183,7 @@ struct WindowBatch {
       g.C = wi.C0; g.c_m = nr; g.c_n = 1;
       gemm_f64(g, s);
     }
-    k_refined<<<1, 32, (nr * (nr + 1) + 2 * b * nr + 3 * nr) * sizeof(double), s>>>(
+    k_refined<<<1, 32, (5 * nr * (nr + 1) + b * nr + 3 * nr) * sizeof(double), s>>>(
         wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
     PP_LAUNCH_CHECK("k_refined");
     sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);
