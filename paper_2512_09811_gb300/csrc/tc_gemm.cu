@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
                       o.s_c0 == 1 && (o.d_c % 8) == 0 && (o.s_r0 % 8) == 0 && (o.s_r1 % 8) == 0 &&
                       (o.s_c1 % 8) == 0 && (!two || (!o2.C && o2.s_c0 == 1 && (o2.d_c % 8) == 0 &&
                                                     (o2.s_r0 % 8) == 0 && (o2.s_r1 % 8) == 0 && (o2.s_c1 % 8) == 0));
+    // single FP32 outputs with the same contiguity: 4 values per store
+    const bool vec4f = o.C && !two && al16(o.C) && o.s_c0 == 1 && (o.d_c % 4) == 0 && (o.s_r0 % 4) == 0 &&
+                       (o.s_r1 % 4) == 0 && (o.s_c1 % 4) == 0;
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + c0, v);
@@ -265,6 +268,27 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
             *reinterpret_cast<uint4 *>(oo.Chi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
             if (oo.Clo) *reinterpret_cast<uint4 *>(oo.Clo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
           }
+        }
+      } else if (row < args.M && vec4f) {
+        for (int g = 0; g < 8; ++g) {
+          const long long col = n0 + c0 + 4 * g;
+          if (col >= args.N) break;
+          if (col + 4 > args.N) {  // ragged tail: element by element
+            for (int q = 0; q < 4 && col + q < args.N; ++q)
+              epi_store(o, rbase + ((col + q) / o.d_c) * o.s_c1 + ((col + q) % o.d_c), o.alpha * v[4 * g + q]);
+            continue;
+          }
+          float4 *dst = reinterpret_cast<float4 *>(o.C + rbase + (col / o.d_c) * o.s_c1 + (col % o.d_c));
+          float4 x = make_float4(o.alpha * v[4 * g], o.alpha * v[4 * g + 1], o.alpha * v[4 * g + 2],
+                                 o.alpha * v[4 * g + 3]);
+          if (o.accumulate) {
+            const float4 y = *dst;
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+          }
+          *dst = x;
         }
       } else if (row < args.M) {
         const long long col = n0 + c0;
