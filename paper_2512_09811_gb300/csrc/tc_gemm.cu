@@ -142,6 +142,7 @@ struct GemmArgs {
   int M, N, nk, nseg;
   GemmOut out, out2;  // out2 is written too when out2.C or out2.Chi is set
   int *err;
+  int ksplit = 1;     // > 1: blockIdx.z takes a share of the K steps and adds into out.C atomically
 };
 __device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float x) {
   if (o.C) {
@@ -180,10 +181,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const int total = args.nseg * args.nk;
+  // this CTA's K steps (all of them unless the reduction is split across blockIdx.z; the host
+  // keeps every share non-empty)
+  const int kb0 = (int)((long long)total * blockIdx.z / args.ksplit);
+  const int kb1 = (int)((long long)total * (blockIdx.z + 1) / args.ksplit);
   if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < total; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int s = (kb - kb0) % STAGES;
+      const uint32_t ph = ((kb - kb0) / STAGES) & 1;
       if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
         atomicExch(args.err, 1);
         abort_flag = 1;
@@ -197,9 +202,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kb = 0; kb < total; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int s = (kb - kb0) % STAGES;
+      const uint32_t ph = ((kb - kb0) / STAGES) & 1;
       if (!mbar_wait(&full_bar[s], ph)) {
         atomicExch(args.err, 2);
         abort_flag = 1;
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
       const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k)
-        mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
       mma_commit(&empty_bar[s]);
     }
     mma_commit(&acc_bar);
@@ -240,7 +245,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + c0, v);
-      if (row < args.M && vec8) {
+      if (row < args.M && args.ksplit > 1) {  // partial sums of a split reduction
+        const long long col = n0 + c0;
+        for (int jj = 0; jj < 32 && col + jj < args.N; ++jj) {
+          const long long cc = col + jj;
+          atomicAdd(o.C + rbase + (cc / o.d_c) * o.s_c1 + (cc % o.d_c) * o.s_c0, o.alpha * v[jj]);
+        }
+      } else if (row < args.M && vec8) {
         for (int g = 0; g < 4; ++g) {
           const long long col = n0 + c0 + 8 * g;
           if (col >= args.N) break;
@@ -355,6 +366,9 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
     fence_barrier_init();
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 256);
+  // the virtual orbital energies of this CTA's d tile, for the denominators of the epilogue
+  __shared__ double eps_d[BM];
+  eps_d[threadIdx.x] = (d0 + (int)threadIdx.x < v) ? args.eps[args.o + d0 + threadIdx.x] : 0.0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -414,16 +428,44 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
     __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + c) * args.ldT + (long long)j * v;
     __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + c) * args.ldT + (long long)j * v : nullptr;
     float *frow = args.Tf ? args.Tf + ((long long)ii * v + c) * args.ldf + (long long)j * v : nullptr;
+    // full 32-column chunks go out 8 BF16 (or 4 FP32) values per 16-byte store; v % 8 == 0
+    // keeps every such chunk 16-byte aligned (ldT and ldf are multiples of 8 and of 4)
+    const bool vec = (v % 8) == 0 && (args.ldT % 8) == 0 && (!frow || (args.ldf % 4) == 0);
     for (int cc = 0; cc < BM; cc += 32) {
       float d1[32], d2[32];
       tmem_ld32(trow + cc, d1);
       tmem_ld32(trow + BM + cc, d2);
-      if (c < v) {
+      if (c < v && vec && d0 + cc + 32 <= v) {
+        float t[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) t[q] = (d1[q] - d2[q]) / (float)(eij_c - eps_d[cc + q]);
+        const int dbase = d0 + cc;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float x0 = t[8 * g + 2 * q], x1 = t[8 * g + 2 * q + 1];
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          *reinterpret_cast<uint4 *>(hrow + dbase + 8 * g) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          if (lrow) *reinterpret_cast<uint4 *>(lrow + dbase + 8 * g) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        if (frow)
+#pragma unroll
+          for (int g = 0; g < 8; ++g)
+            *reinterpret_cast<float4 *>(frow + dbase + 4 * g) =
+                make_float4(t[4 * g], t[4 * g + 1], t[4 * g + 2], t[4 * g + 3]);
+      } else if (c < v) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const int d = d0 + cc + q;
           if (d < v) {
-            const float t = (d1[q] - d2[q]) / (float)(eij_c - args.eps[o + d]);
+            const float t = (d1[q] - d2[q]) / (float)(eij_c - eps_d[cc + q]);
             const __nv_bfloat16 h = __float2bfloat16_rn(t);
             hrow[d] = h;
             if (lrow) lrow[d] = __float2bfloat16_rn(t - __bfloat162float(h));
@@ -572,6 +614,15 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
   }
   GemmArgs a{M, N, (int)(K / BK), nseg, out, out2 ? *out2 : GemmOut{}, err};
   dim3 grid((M + BM - 1) / BM, (N + GEMM_BN - 1) / GEMM_BN);
+  // few output tiles over a long reduction (an accumulating FP32 output): split K across
+  // CTAs so that about two waves of the GPU share it, each taking at least 8 K steps
+  if (out.C && out.accumulate && !out2) {
+    const long long tiles = (long long)grid.x * grid.y, steps = (long long)nseg * a.nk;
+    long long ks = std::min<long long>(304 / std::max<long long>(tiles, 1), steps / 8);
+    ks = std::max<long long>(1, std::min<long long>(ks, 65535));
+    a.ksplit = (int)ks;
+    grid.z = (unsigned)ks;
+  }
   if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
   k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
