@@ -29,7 +29,11 @@ template <class T> struct SigmaWork {
 template <class T> struct SigmaHooks {
   std::function<bool(int R, const T *V, T *W)> w;                 // W[r][j][Q][d] = (V_r Bvv_Q)[j][d]
   std::function<bool(int R, const T *V, T *EF, bool second)> ef;  // E (and F) into EF[r][t][i][j]
+  // Cmat == nullptr: C_Q(V) was already formed by first_order in the amplitude hook's own layout
   std::function<void(int R, const T *Cmat, T *Bacc)> amplitude;
+  // the whole first-order block (W, KA, E/F, KB and, at second order, C_Q(V)) in one go;
+  // returns false to fall back to the step-by-step contractions below
+  std::function<bool(int R, T *Aacc, T *Bacc)> first_order;
 };
 
 namespace sigma_detail {
@@ -150,64 +154,68 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     gemm<T>(j, s);
     j.C = Bacc;
     gemm<T>(j, s);
-    T *W = wk.W;  // W[r][j][Q][d] = V_r BvvP
-    const long long oQv = (long long)o * Q * v;
-    if (!(hk.w && hk.w(R, V, W))) {
-      GemmS<T> w;
-      w.M = o; w.N = Q * v; w.K = v; w.nbatch = R;
-      w.A = V; w.a_m = v; w.a_k = 1; w.a_batch = ov;
-      w.B = res.BvvP; w.b_k = (long long)Q * v; w.b_n = 1;
-      w.C = W; w.c_m = (long long)Q * v; w.c_n = 1; w.c_batch = oQv;
-      gemm<T>(w, s);
-    }
-    GemmS<T> ka;  // KA: Aacc -= sum_Q sum_k Boo[Q][i][k] W[r][k][Q][a]
-    ka.M = o; ka.N = v; ka.K = o; ka.nred = Q; ka.nbatch = R;
-    ka.A = res.Boo; ka.a_m = o; ka.a_k = 1; ka.a_red = (long long)o * o;
-    ka.B = W; ka.b_k = (long long)Q * v; ka.b_n = 1; ka.b_red = v; ka.b_batch = oQv;
-    ka.C = Aacc; ka.c_m = v; ka.c_n = 1; ka.c_batch = ov; ka.alpha = T(-1); ka.beta = T(1);
-    if (split_k<T>()) ka.ksplit = 16;
-    gemm<T>(ka, s);
-    T *EF = wk.EF;  // E[r][Q][i][j] = sum_b Bov[Q][i][b] V[r][j][b]; F likewise with Gam
-    const long long efb = 2LL * Q * o * o;
-    if (!(hk.ef && hk.ef(R, V, EF, order >= 2))) {
-      GemmS<T> e;
-      e.M = Q * o; e.N = o; e.K = v; e.nbatch = R;
-      e.A = res.Bov; e.a_m = v; e.a_k = 1;
-      e.B = V; e.b_k = 1; e.b_n = v; e.b_batch = ov;
-      e.C = EF; e.c_m = o; e.c_n = 1; e.c_batch = efb;
-      gemm<T>(e, s);
-      if (order >= 2) {
-        e.A = res.Gam;
-        e.C = EF + (long long)Q * o * o;
-        gemm<T>(e, s);
-      }
-    }
-    GemmS<T> kb;  // Bacc -= sum_t sum_j EF[r][t][i][j] GB[t][j][a]
-    kb.M = o; kb.N = v; kb.K = o; kb.nbatch = R;
-    kb.A = EF; kb.a_m = o; kb.a_k = 1; kb.a_red = (long long)o * o; kb.a_batch = efb;
-    kb.b_k = v; kb.b_n = 1; kb.b_red = ov;
-    kb.C = Bacc; kb.c_m = v; kb.c_n = 1; kb.c_batch = ov; kb.alpha = T(-1); kb.beta = T(1);
-    if (order >= 2) {
-      kb.nred = 2 * Q;
-      kb.B = res.GB;
+    if (hk.first_order && hk.first_order(R, Aacc, Bacc)) {
+      if (order >= 2) hk.amplitude(R, nullptr, Bacc);
     } else {
-      kb.nred = Q;
-      kb.B = res.Bov;
-    }
-    if (split_k<T>()) kb.ksplit = 16;
-    gemm<T>(kb, s);
-    if (order >= 2) {
-      T *U = wk.U;  // U[r][Q][l][b] = Boo_Q V_r, then C_Q(V) = W - U in place
-      const long long qov = (long long)Q * ov;
-      GemmS<T> u;
-      u.M = Q * o; u.N = v; u.K = o; u.nbatch = R;
-      u.A = res.Boo; u.a_m = o; u.a_k = 1;
-      u.B = V; u.b_k = v; u.b_n = 1; u.b_batch = ov;
-      u.C = U; u.c_m = v; u.c_n = 1; u.c_batch = qov;
-      gemm<T>(u, s);
-      k_cmat<T><<<ew_grid(R * qov), 256, 0, s>>>(U, W, o, v, Q, R * qov);
-      PP_LAUNCH_CHECK("k_cmat");
-      hk.amplitude(R, (const T *)U, Bacc);
+      T *W = wk.W;  // W[r][j][Q][d] = V_r BvvP
+      const long long oQv = (long long)o * Q * v;
+      if (!(hk.w && hk.w(R, V, W))) {
+        GemmS<T> w;
+        w.M = o; w.N = Q * v; w.K = v; w.nbatch = R;
+        w.A = V; w.a_m = v; w.a_k = 1; w.a_batch = ov;
+        w.B = res.BvvP; w.b_k = (long long)Q * v; w.b_n = 1;
+        w.C = W; w.c_m = (long long)Q * v; w.c_n = 1; w.c_batch = oQv;
+        gemm<T>(w, s);
+      }
+      GemmS<T> ka;  // KA: Aacc -= sum_Q sum_k Boo[Q][i][k] W[r][k][Q][a]
+      ka.M = o; ka.N = v; ka.K = o; ka.nred = Q; ka.nbatch = R;
+      ka.A = res.Boo; ka.a_m = o; ka.a_k = 1; ka.a_red = (long long)o * o;
+      ka.B = W; ka.b_k = (long long)Q * v; ka.b_n = 1; ka.b_red = v; ka.b_batch = oQv;
+      ka.C = Aacc; ka.c_m = v; ka.c_n = 1; ka.c_batch = ov; ka.alpha = T(-1); ka.beta = T(1);
+      if (split_k<T>()) ka.ksplit = 16;
+      gemm<T>(ka, s);
+      T *EF = wk.EF;  // E[r][Q][i][j] = sum_b Bov[Q][i][b] V[r][j][b]; F likewise with Gam
+      const long long efb = 2LL * Q * o * o;
+      if (!(hk.ef && hk.ef(R, V, EF, order >= 2))) {
+        GemmS<T> e;
+        e.M = Q * o; e.N = o; e.K = v; e.nbatch = R;
+        e.A = res.Bov; e.a_m = v; e.a_k = 1;
+        e.B = V; e.b_k = 1; e.b_n = v; e.b_batch = ov;
+        e.C = EF; e.c_m = o; e.c_n = 1; e.c_batch = efb;
+        gemm<T>(e, s);
+        if (order >= 2) {
+          e.A = res.Gam;
+          e.C = EF + (long long)Q * o * o;
+          gemm<T>(e, s);
+        }
+      }
+      GemmS<T> kb;  // Bacc -= sum_t sum_j EF[r][t][i][j] GB[t][j][a]
+      kb.M = o; kb.N = v; kb.K = o; kb.nbatch = R;
+      kb.A = EF; kb.a_m = o; kb.a_k = 1; kb.a_red = (long long)o * o; kb.a_batch = efb;
+      kb.b_k = v; kb.b_n = 1; kb.b_red = ov;
+      kb.C = Bacc; kb.c_m = v; kb.c_n = 1; kb.c_batch = ov; kb.alpha = T(-1); kb.beta = T(1);
+      if (order >= 2) {
+        kb.nred = 2 * Q;
+        kb.B = res.GB;
+      } else {
+        kb.nred = Q;
+        kb.B = res.Bov;
+      }
+      if (split_k<T>()) kb.ksplit = 16;
+      gemm<T>(kb, s);
+      if (order >= 2) {
+        T *U = wk.U;  // U[r][Q][l][b] = Boo_Q V_r, then C_Q(V) = W - U in place
+        const long long qov = (long long)Q * ov;
+        GemmS<T> u;
+        u.M = Q * o; u.N = v; u.K = o; u.nbatch = R;
+        u.A = res.Boo; u.a_m = o; u.a_k = 1;
+        u.B = V; u.b_k = v; u.b_n = 1; u.b_batch = ov;
+        u.C = U; u.c_m = v; u.c_n = 1; u.c_batch = qov;
+        gemm<T>(u, s);
+        k_cmat<T><<<ew_grid(R * qov), 256, 0, s>>>(U, W, o, v, Q, R * qov);
+        PP_LAUNCH_CHECK("k_cmat");
+        hk.amplitude(R, (const T *)U, Bacc);
+      }
     }
   }
   if (order >= 2) {

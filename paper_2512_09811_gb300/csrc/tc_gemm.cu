@@ -137,6 +137,8 @@ struct GemmOut {
   __nv_bfloat16 *Chi = nullptr, *Clo = nullptr;
   float alpha = 1.f;
   int accumulate = 0;
+  const float *add = nullptr;  // optional FP32 addend at the same offsets, times add_scale
+  float add_scale = 0.f;
 };
 struct GemmArgs {
   int M, N, nk, nseg;
@@ -153,6 +155,78 @@ __device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float
     if (o.Clo) o.Clo[off] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
+
+// 32 consecutive columns [col0, col0 + 32) of one output row: x = alpha acc (+ add_scale add[off])
+// written as FP32 (optionally accumulated) or as a BF16 pair.  Columns that run contiguously
+// (s_c0 == 1) in 16-byte-aligned groups go out 8 BF16 / 4 FP32 values per store.
+__device__ __forceinline__ bool al16(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+__device__ void store_row32(const GemmOut &o, long long rbase, long long col0, const float *v, int N) {
+  const bool contig = o.s_c0 == 1 && (o.s_r0 % 8) == 0 && (o.s_r1 % 8) == 0 && (o.s_c1 % 8) == 0 &&
+                      (o.d_c % 8) == 0 && (!o.add || al16(o.add));
+  if (!o.C && contig && al16(o.Chi) && al16(o.Clo)) {
+    for (int g = 0; g < 4; ++g) {
+      const long long col = col0 + 8 * g;
+      if (col >= N) return;
+      const long long off = rbase + (col / o.d_c) * o.s_c1 + (col % o.d_c);
+      if (col + 8 > N) {  // ragged tail
+        for (int q = 0; q < 8 && col + q < N; ++q)
+          epi_store(o, off + q, o.alpha * v[8 * g + q] + (o.add ? o.add_scale * o.add[off + q] : 0.f));
+        return;
+      }
+      float x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = o.alpha * v[8 * g + q];
+      if (o.add) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(o.add + off);
+        const float4 a1 = *reinterpret_cast<const float4 *>(o.add + off + 4);
+        x[0] += o.add_scale * a0.x; x[1] += o.add_scale * a0.y; x[2] += o.add_scale * a0.z; x[3] += o.add_scale * a0.w;
+        x[4] += o.add_scale * a1.x; x[5] += o.add_scale * a1.y; x[6] += o.add_scale * a1.z; x[7] += o.add_scale * a1.w;
+      }
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
+        hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      *reinterpret_cast<uint4 *>(o.Chi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if (o.Clo) *reinterpret_cast<uint4 *>(o.Clo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    return;
+  }
+  if (o.C && contig && al16(o.C) && !o.add) {
+    for (int g = 0; g < 8; ++g) {
+      const long long col = col0 + 4 * g;
+      if (col >= N) return;
+      const long long off = rbase + (col / o.d_c) * o.s_c1 + (col % o.d_c);
+      if (col + 4 > N) {
+        for (int q = 0; q < 4 && col + q < N; ++q) epi_store(o, off + q, o.alpha * v[4 * g + q]);
+        return;
+      }
+      float4 *dst = reinterpret_cast<float4 *>(o.C + off);
+      float4 x = make_float4(o.alpha * v[4 * g], o.alpha * v[4 * g + 1], o.alpha * v[4 * g + 2], o.alpha * v[4 * g + 3]);
+      if (o.accumulate) {
+        const float4 y = *dst;
+        x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+      }
+      *dst = x;
+    }
+    return;
+  }
+  long long cb = col0 / o.d_c, cr = col0 % o.d_c;
+  for (int j = 0; j < 32; ++j) {
+    if (col0 + j >= N) return;
+    const long long off = rbase + cb * o.s_c1 + cr * o.s_c0;
+    epi_store(o, off, o.alpha * v[j] + (o.add ? o.add_scale * o.add[off] : 0.f));
+    if (++cr == o.d_c) {
+      cr = 0;
+      ++cb;
+    }
+  }
+}
+
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ GemmMaps maps, GemmArgs args) {
@@ -232,95 +306,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const long long rbase = (row / o.d_r) * o.s_r1 + (row % o.d_r) * o.s_r0;
     const long long rbase2 = two ? (row / o2.d_r) * o2.s_r1 + (row % o2.d_r) * o2.s_r0 : 0;
-    // BF16-pair outputs whose columns run contiguously in groups of 8 (16-byte aligned) are
-    // written 8 values per store
-    auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    const bool vec8 = !o.C && al16(o.Chi) && al16(o.Clo) && (!two || (al16(o2.Chi) && al16(o2.Clo))) &&
-                      o.s_c0 == 1 && (o.d_c % 8) == 0 && (o.s_r0 % 8) == 0 && (o.s_r1 % 8) == 0 &&
-                      (o.s_c1 % 8) == 0 && (!two || (!o2.C && o2.s_c0 == 1 && (o2.d_c % 8) == 0 &&
-                                                    (o2.s_r0 % 8) == 0 && (o2.s_r1 % 8) == 0 && (o2.s_c1 % 8) == 0));
-    // single FP32 outputs with the same contiguity: 4 values per store
-    const bool vec4f = o.C && !two && al16(o.C) && o.s_c0 == 1 && (o.d_c % 4) == 0 && (o.s_r0 % 4) == 0 &&
-                       (o.s_r1 % 4) == 0 && (o.s_c1 % 4) == 0;
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + c0, v);
-      if (row < args.M && args.ksplit > 1) {  // partial sums of a split reduction
-        const long long col = n0 + c0;
+      if (row >= args.M) continue;
+      const long long col = n0 + c0;
+      if (args.ksplit > 1) {  // partial sums of a split reduction
         for (int jj = 0; jj < 32 && col + jj < args.N; ++jj) {
           const long long cc = col + jj;
           atomicAdd(o.C + rbase + (cc / o.d_c) * o.s_c1 + (cc % o.d_c) * o.s_c0, o.alpha * v[jj]);
         }
-      } else if (row < args.M && vec8) {
-        for (int g = 0; g < 4; ++g) {
-          const long long col = n0 + c0 + 8 * g;
-          if (col >= args.N) break;
-          if (col + 8 > args.N) {  // ragged tail: element by element
-            for (int q = 0; q < 8 && col + q < args.N; ++q) {
-              const long long cc = col + q;
-              epi_store(o, rbase + (cc / o.d_c) * o.s_c1 + (cc % o.d_c), o.alpha * v[8 * g + q]);
-              if (two) epi_store(o2, rbase2 + (cc / o2.d_c) * o2.s_c1 + (cc % o2.d_c), o2.alpha * v[8 * g + q]);
-            }
-            continue;
-          }
-          for (int t = 0; t < (two ? 2 : 1); ++t) {
-            const GemmOut &oo = t ? o2 : o;
-            const long long off = (t ? rbase2 : rbase) + (col / oo.d_c) * oo.s_c1 + (col % oo.d_c);
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float x0 = oo.alpha * v[8 * g + 2 * q], x1 = oo.alpha * v[8 * g + 2 * q + 1];
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-              const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-              const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-              hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-              lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-            *reinterpret_cast<uint4 *>(oo.Chi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            if (oo.Clo) *reinterpret_cast<uint4 *>(oo.Clo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          }
-        }
-      } else if (row < args.M && vec4f) {
-        for (int g = 0; g < 8; ++g) {
-          const long long col = n0 + c0 + 4 * g;
-          if (col >= args.N) break;
-          if (col + 4 > args.N) {  // ragged tail: element by element
-            for (int q = 0; q < 4 && col + q < args.N; ++q)
-              epi_store(o, rbase + ((col + q) / o.d_c) * o.s_c1 + ((col + q) % o.d_c), o.alpha * v[4 * g + q]);
-            continue;
-          }
-          float4 *dst = reinterpret_cast<float4 *>(o.C + rbase + (col / o.d_c) * o.s_c1 + (col % o.d_c));
-          float4 x = make_float4(o.alpha * v[4 * g], o.alpha * v[4 * g + 1], o.alpha * v[4 * g + 2],
-                                 o.alpha * v[4 * g + 3]);
-          if (o.accumulate) {
-            const float4 y = *dst;
-            x.x += y.x;
-            x.y += y.y;
-            x.z += y.z;
-            x.w += y.w;
-          }
-          *dst = x;
-        }
-      } else if (row < args.M) {
-        const long long col = n0 + c0;
-        long long cb = col / o.d_c, cr = col % o.d_c;
-        long long cb2 = two ? col / o2.d_c : 0, cr2 = two ? col % o2.d_c : 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (col + j < args.N) {
-            epi_store(o, rbase + cb * o.s_c1 + cr * o.s_c0, o.alpha * v[j]);
-            if (two) epi_store(o2, rbase2 + cb2 * o2.s_c1 + cr2 * o2.s_c0, o2.alpha * v[j]);
-          }
-          if (++cr == o.d_c) {
-            cr = 0;
-            ++cb;
-          }
-          if (two && ++cr2 == o2.d_c) {
-            cr2 = 0;
-            ++cb2;
-          }
-        }
+        continue;
       }
+      store_row32(o, rbase, col, v, args.N);
+      if (two) store_row32(o2, rbase2, col, v, args.N);
     }
   }
   tc_fence_before();
@@ -530,6 +529,46 @@ __global__ void k_d2f(const double *__restrict__ s, float *__restrict__ d, long 
     d[p] = (float)s[p];
 }
 
+// vT[(r,b)][k] = V[r][k][b] (k < o; zero up to ldk), V double [R][o][v], as a BF16 pair
+__global__ void k_vT(const double *__restrict__ V, int R, int o, int v, long long ldk, __nv_bfloat16 *__restrict__ hi,
+                     __nv_bfloat16 *__restrict__ lo) {
+  const long long total = (long long)R * v * ldk;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long rb = p / ldk, k = p % ldk;
+    const long long r = rb / v, b = rb % v;
+    const float x = (k < o) ? (float)V[(r * o + k) * v + b] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    if (lo) lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+// booR[i][(Q,k)] = Boo[Q][i][k] (zero up to ldk), Boo double [Q][o][o], as a BF16 pair
+__global__ void k_boo_r(const double *__restrict__ Boo, int Q, int o, long long ldk, __nv_bfloat16 *__restrict__ hi,
+                        __nv_bfloat16 *__restrict__ lo) {
+  const long long total = (long long)o * ldk;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long i = p / ldk, qk = p % ldk;
+    const float x = (qk < (long long)Q * o) ? (float)Boo[((qk / o) * o + i) * o + qk % o] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+// gbT[a][(t,j)] = GB[t][j][a] for t < nt (zero up to ldk), GB double [nt][o][v], as a BF16 pair
+__global__ void k_gb_t(const double *__restrict__ GB, int nt, int o, int v, long long ldk, __nv_bfloat16 *__restrict__ hi,
+                       __nv_bfloat16 *__restrict__ lo) {
+  const long long total = (long long)v * ldk;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long a = p / ldk, tj = p % ldk;
+    const float x = (tj < (long long)nt * o) ? (float)GB[tj * v + a] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[p] = h;
+    lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
 __global__ void k_f2d(const float *__restrict__ s, double *__restrict__ d, long long n) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x)
@@ -672,6 +711,10 @@ struct TcPlan {
   DevBuf gam_hi, gam_lo;     // [(Q,i)][vp]        F = Gam_Q V^T
   DevBuf bvvT_hi, bvvT_lo;   // [a][(c,Qp)]        sum_Q P_Q Bvv_Q
   DevBuf booT_hi, booT_lo;   // [i][(k,Qp)]        sum_Q Boo_Q P_Q
+  long long kbo = 0, kqo = 0, kef = 0;  // padded K of the U, KA and KB contractions
+  DevBuf booK_hi, booK_lo;   // [(Q,l)][kbo]       U = Boo_Q V
+  DevBuf booR_hi, booR_lo;   // [i][(Q,k)]         KA = sum_Q Boo_Q W_Q
+  DevBuf gbT_hi, gbT_lo;     // [a][(t,j)]         KB = sum_t EF_t GB_t
   // FP32 copies of the operands of the remaining SIMT contractions
   DevBuf f_gap, f_eps, f_Bov, f_Boo, f_Bvv, f_BvvP, f_BooT, f_GB, f_Gam, f_poo, f_qoo, f_pvv, f_qvv;
   // workspaces
@@ -681,6 +724,10 @@ struct TcPlan {
   DevBuf t_hi, t_lo;         // amplitude slab [rows][ldT]
   DevBuf p1_hi, p1_lo;       // P as [(r,i)][(c,Qp)]
   DevBuf p2_hi, p2_lo;       // P as [(r,a)][(k,Qp)]
+  DevBuf vT_hi, vT_lo;       // V^T [(r,b)][kbo]
+  DevBuf uC;                 // U = Boo_Q V (FP32) in the layout of C_Q(V)
+  DevBuf kaB_hi, kaB_lo;     // W as [(r,a)][(Q,k)]
+  DevBuf efB_hi, efB_lo;     // E, F as [(r,i)][(t,j)]
   DevBuf err;
 };
 
@@ -692,7 +739,9 @@ size_t tc_plan_bytes(const pp_ctx *c) {
                           &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
                           &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                           &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
-                          &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err};
+                          &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
+                          &p->booR_hi, &p->booR_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                          &p->kaB_hi, &p->kaB_lo, &p->efB_hi, &p->efB_lo};
   size_t n = 0;
   for (const DevBuf *b : bufs) n += b->bytes;
   return n;
@@ -706,7 +755,9 @@ void tc_destroy(pp_ctx *c) {
                     &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
                     &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                     &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
-                    &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err};
+                    &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
+                    &p->booR_hi, &p->booR_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                    &p->kaB_hi, &p->kaB_lo, &p->efB_hi, &p->efB_lo};
   for (DevBuf *b : bufs) b->release();
   for (auto &v : p->prof.ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -785,10 +836,20 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   f32_copy(p->f_Bvv, c->Bvv, Q * v * v, s);
   f32_copy(p->f_BvvP, c->BvvP, Q * v * v, s);
   f32_copy(p->f_BooT, c->BooT, Q * o * o, s);
+  p->kbo = pad64(o);
+  p->kqo = pad64(Q * o);
+  p->kef = pad64(2 * Q * o);
   if (c->opt.order >= 1 && Q > 0) {
     bf16_pair(p->bvv_hi, p->bvv_lo, c->Bvv.as<double>(), Q * v, v, v, p->vp, s);
     bf16_pair(p->bov_hi, p->bov_lo, c->Bov.as<double>(), Q * o, v, v, p->vp, s);
+    p->booR_hi.ensure(sizeof(__nv_bfloat16) * (size_t)o * p->kqo);
+    p->booR_lo.ensure(sizeof(__nv_bfloat16) * (size_t)o * p->kqo);
+    tc::k_boo_r<<<tc::grid_for(o * p->kqo), 256, 0, s>>>(c->Boo.as<double>(), (int)Q, (int)o, p->kqo,
+                                                         p->booR_hi.as<__nv_bfloat16>(), p->booR_lo.as<__nv_bfloat16>());
+    PP_LAUNCH_CHECK("k_boo_r");
   }
+  if (c->opt.order >= 2 && Q > 0)
+    bf16_pair(p->booK_hi, p->booK_lo, c->Boo.as<double>(), Q * o, o, o, p->kbo, s);
   if (c->opt.order >= 2 && Q > 0) {
     p->bovT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
     p->bovT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
@@ -834,7 +895,14 @@ static TcPlan *tc_plan(pp_ctx *c) {
   f32_copy(p->f_qoo, c->q_oo, o * o, s);
   f32_copy(p->f_pvv, c->p_vv, v * v, s);
   f32_copy(p->f_qvv, c->q_vv, v * v, s);
-  if (c->opt.order >= 1 && Q > 0) bf16_pair(p->gam_hi, p->gam_lo, c->Gam.as<double>(), Q * o, v, v, p->vp, s);
+  if (c->opt.order >= 1 && Q > 0) {
+    bf16_pair(p->gam_hi, p->gam_lo, c->Gam.as<double>(), Q * o, v, v, p->vp, s);
+    p->gbT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)v * p->kef);
+    p->gbT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)v * p->kef);
+    tc::k_gb_t<<<tc::grid_for(v * p->kef), 256, 0, s>>>(c->GB.as<double>(), (int)(2 * Q), (int)o, (int)v, p->kef,
+                                                        p->gbT_hi.as<__nv_bfloat16>(), p->gbT_lo.as<__nv_bfloat16>());
+    PP_LAUNCH_CHECK("k_gb_t");
+  }
   p->ready = true;
   return p;
 }
@@ -956,15 +1024,20 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
   p->w_tmp.ensure(sizeof(float) * 4 * (size_t)Rmax * ov);
   if (c->opt.order >= 1) {
     p->w_cq.ensure(sizeof(float) * (size_t)Q * Rmax);
-    p->w_W.ensure(sizeof(float) * (size_t)Rmax * o * Q * v);
-    p->w_EF.ensure(sizeof(float) * (size_t)Rmax * 2 * Q * o * o);
     p->v_hi.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
     p->v_lo.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
+    // K paddings (and, at first order, the F half of EF) stay zero: never written
+    ensure_zeroed(p->kaB_hi, sizeof(bf) * (size_t)Rmax * v * p->kqo, s);
+    ensure_zeroed(p->kaB_lo, sizeof(bf) * (size_t)Rmax * v * p->kqo, s);
+    ensure_zeroed(p->efB_hi, sizeof(bf) * (size_t)Rmax * o * p->kef, s);
+    ensure_zeroed(p->efB_lo, sizeof(bf) * (size_t)Rmax * o * p->kef, s);
   }
   if (c->opt.order >= 2) {
-    p->w_U.ensure(sizeof(float) * (size_t)Rmax * Q * ov);
-    p->c_hi.ensure(sizeof(bf) * (size_t)Rmax * Q * ldT);
-    p->c_lo.ensure(sizeof(bf) * (size_t)Rmax * Q * ldT);
+    p->vT_hi.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
+    p->vT_lo.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
+    p->uC.ensure(sizeof(float) * (size_t)Rmax * Q * ldT);
+    ensure_zeroed(p->c_hi, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
+    ensure_zeroed(p->c_lo, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
     p->t_hi.ensure(sizeof(bf) * (size_t)p->slab_i * v * ldT);
     p->t_lo.ensure(sizeof(bf) * (size_t)p->slab_i * v * ldT);
     const size_t pbytes = sizeof(bf) * (size_t)Rmax * ov * Qp;  // padding columns stay zero
@@ -997,43 +1070,119 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       PP_LAUNCH_CHECK("k_to_bf16");
     }
     SigmaWork<float> wk{p->w_acc.as<float>(), p->w_acc.as<float>() + (long long)R * ov, p->w_tmp.as<float>(),
-                        p->w_cq.as<float>(), p->w_W.as<float>(), p->w_U.as<float>(), p->w_EF.as<float>()};
+                        p->w_cq.as<float>(), nullptr, nullptr, nullptr};  // W, U, EF: first_order
     SigmaHooks<float> hk;
-    hk.w = [&](int Rc, const float *, float *W) {
-      // W[(r,j)][(Q,d)] = sum_b V[(r,j)][b] Bvv[(Q,d)][b]
+    // The first-order block on the tensor cores; its operands are written by the GEMMs that
+    // produce them in the K-major layouts the next GEMM reads.  These contractions are small
+    // next to the amplitude contraction and always run in the split form (three BF16
+    // products, FP32-level), so the BF16 phase keeps its first-order terms at that accuracy.
+    hk.first_order = [&](int Rc, float *Aacc, float *Bacc) {
+      const int nseg1 = 3;
+      const int order = c->opt.order;
+      const long long kbo = p->kbo, kqo = p->kqo, kef = p->kef;
+      bf *kah = p->kaB_hi.as<bf>(), *kal = p->kaB_lo.as<bf>();
+      bf *efh = p->efB_hi.as<bf>(), *efl = p->efB_lo.as<bf>();
       const bf *A[3], *B[3];
-      seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
-      tc::GemmOut out;
-      out.C = W;
-      out.s_r0 = (long long)Q * v;
-      tc::gemm_bf16(Rc * o, Q * v, vp, nseg, A, vp, B, vp, out, err, s);
-      return true;
-    };
-    hk.ef = [&](int Rc, const float *, float *EF, bool second) {
-      // EF[r][t][i][j] = sum_b X_t[i][b] V_r[j][b] with X = Bov (t < Q) and Gam (t >= Q)
-      const bf *A[3], *B[3];
-      tc::GemmOut out;
-      out.d_r = o;
-      out.s_r1 = (long long)o * o;
-      out.s_r0 = o;
-      out.d_c = o;
-      out.s_c1 = 2LL * Q * o * o;
-      out.s_c0 = 1;
-      out.C = EF;
-      seg3(p->bov_hi.as<bf>(), p->bov_lo.as<bf>(), vhi, vlo, A, B);
-      tc::gemm_bf16(Q * o, Rc * o, vp, nseg, A, vp, B, vp, out, err, s);
-      if (second) {
-        out.C = EF + (long long)Q * o * o;
-        seg3(p->gam_hi.as<bf>(), p->gam_lo.as<bf>(), vhi, vlo, A, B);
-        tc::gemm_bf16(Q * o, Rc * o, vp, nseg, A, vp, B, vp, out, err, s);
+      if (order >= 2) {
+        // U[r][Q][l][b] = sum_k Boo[Q][l][k] V[r][k][b]: rows (Q,l), columns (r,b), K = k; FP32 in
+        // the layout of C_Q(V), [(r,Q)][(l,b)] with row stride ldT
+        tc::k_vT<<<tc::grid_for((long long)Rc * v * kbo), 256, 0, s>>>(V64, Rc, o, v, kbo, p->vT_hi.as<bf>(),
+                                                                      p->vT_lo.as<bf>());
+        PP_LAUNCH_CHECK("k_vT");
+        seg3(p->booK_hi.as<bf>(), p->booK_lo.as<bf>(), p->vT_hi.as<bf>(), p->vT_lo.as<bf>(), A, B);
+        tc::GemmOut u;
+        u.C = p->uC.as<float>();
+        u.d_r = o;
+        u.s_r1 = ldT;
+        u.s_r0 = v;
+        u.d_c = v;
+        u.s_c1 = (long long)Q * ldT;
+        u.s_c0 = 1;
+        tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, u, err, s);
+      }
+      // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d).  Written as
+      // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction and as
+      // [(r,a)][(Q,k)] for KA
+      {
+        seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
+        tc::GemmOut ka;
+        ka.Chi = kah;
+        ka.Clo = kal;
+        ka.d_r = o;
+        ka.s_r1 = (long long)v * kqo;
+        ka.s_r0 = 1;
+        ka.d_c = v;
+        ka.s_c1 = o;
+        ka.s_c0 = kqo;
+        if (order >= 2) {
+          tc::GemmOut cc;
+          cc.Chi = p->c_hi.as<bf>();
+          cc.Clo = split ? p->c_lo.as<bf>() : nullptr;
+          cc.d_r = o;
+          cc.s_r1 = (long long)Q * ldT;
+          cc.s_r0 = v;
+          cc.d_c = v;
+          cc.s_c1 = ldT;
+          cc.s_c0 = 1;
+          cc.add = p->uC.as<float>();
+          cc.add_scale = -1.f;
+          tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s, &ka);
+        } else {
+          tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, ka, err, s);
+        }
+      }
+      // KA: Aacc[r][i][a] -= sum_(Q,k) Boo[Q][i][k] W[r][k][Q][a]   (rows i, columns (r,a))
+      {
+        seg3(p->booR_hi.as<bf>(), p->booR_lo.as<bf>(), kah, kal, A, B);
+        tc::GemmOut out;
+        out.C = Aacc;
+        out.s_r0 = v;
+        out.d_c = v;
+        out.s_c1 = ov;
+        out.s_c0 = 1;
+        out.alpha = -1.f;
+        out.accumulate = 1;
+        tc::gemm_bf16(o, Rc * v, kqo, nseg1, A, kqo, B, kqo, out, err, s);
+      }
+      // E and F: EF[(r,i)][(t,j)] = sum_b X_t[i][b] V[r][j][b], X = Bov (t < Q), Gamma (t >= Q)
+      {
+        tc::GemmOut out;
+        out.Chi = efh;
+        out.Clo = efl;
+        out.d_r = o;
+        out.s_r1 = o;
+        out.s_r0 = kef;
+        out.d_c = o;
+        out.s_c1 = (long long)o * kef;
+        out.s_c0 = 1;
+        seg3(p->bov_hi.as<bf>(), p->bov_lo.as<bf>(), vhi, vlo, A, B);
+        tc::gemm_bf16(Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
+        if (order >= 2) {
+          out.Chi = efh + (long long)Q * o;
+          out.Clo = efl ? efl + (long long)Q * o : nullptr;
+          seg3(p->gam_hi.as<bf>(), p->gam_lo.as<bf>(), vhi, vlo, A, B);
+          tc::gemm_bf16(Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
+        }
+      }
+      // KB: Bacc[r][i][a] -= sum_(t,j) EF[r][t][i][j] GB[t][j][a]   (rows (r,i), columns a)
+      {
+        seg3(efh, efl, p->gbT_hi.as<bf>(), p->gbT_lo.as<bf>(), A, B);
+        tc::GemmOut out;
+        out.C = Bacc;
+        out.s_r0 = v;
+        out.alpha = -1.f;
+        out.accumulate = 1;
+        tc::gemm_bf16(Rc * o, v, kef, nseg1, A, kef, B, kef, out, err, s);
       }
       return true;
     };
     hk.amplitude = [&](int Rc, const float *Cmat, float *Bacc) {
       const long long NC = (long long)Rc * Q;
       bf *chi = p->c_hi.as<bf>(), *clo = p->c_lo.as<bf>();
-      tc::k_to_bf16<float><<<tc::grid_for(NC * ldT), 256, 0, s>>>(Cmat, NC, ov, ov, chi, clo, ldT);
-      PP_LAUNCH_CHECK("k_to_bf16");
+      if (Cmat) {  // C_Q(V) from the step-by-step path: convert to the BF16 pair
+        tc::k_to_bf16<float><<<tc::grid_for(NC * ldT), 256, 0, s>>>(Cmat, NC, ov, ov, chi, clo, ldT);
+        PP_LAUNCH_CHECK("k_to_bf16");
+      }
       bf *thi = p->t_hi.as<bf>();
       bf *tlo = split ? p->t_lo.as<bf>() : nullptr;
       bf *p1h = p->p1_hi.as<bf>(), *p1l = split ? p->p1_lo.as<bf>() : nullptr;
