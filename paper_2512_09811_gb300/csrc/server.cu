@@ -70,8 +70,9 @@ size_t estimate_bytes(long long o, long long v, long long Q, const pp_options &o
   if (opt.prec != PP_FP64) {
     const long long ldq = pad(Q), ldT = pad(ov), vp = pad(v), Qp = pad(Q);
     total += 4 * (ov + n + Q * ov + 2 * Q * o * o + 2 * Q * v * v + 3 * Q * ov + 2 * o * o + 2 * v * v);
-    total += 4 * (ov * ldq + Q * v * vp + 2 * Q * o * vp + v * v * Qp + o * o * Qp);
-    const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 4 * Q * ldT + 8 * ov * Qp;
+    total += 4 * (ov * ldq + Q * v * vp + 2 * Q * o * vp + v * v * Qp + o * o * Qp + v * pad(Q * v));
+    const long long per_half =
+        4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 4 * Q * ldT + 8 * ov * Qp + 4 * o * pad(Q * v);
     const long long ws = (long long)(opt.workspace_gb * (1LL << 30));
     long long R = std::max<long long>(2, std::min<long long>(ws / std::max<long long>(per_half, 1), 64));
     R = std::min(R & ~1LL, rows_max);

@@ -434,67 +434,60 @@ __global__ void k_unit_vectors(double *__restrict__ V, long long L, const int *_
 }
 
 
-// ---- small dense linear algebra on the projected pencil (one CTA) -------------------
-// Cholesky of a symmetric positive definite m x m matrix held in shared memory
-// (row stride ld), computed by warp 0.  Lower factor in place; diag in dL.
-// Returns false (uniformly on warp 0) if a pivot is not positive.
-__device__ bool warp_cholesky(double *G, int ld, int m, double *dL) {
-  const int lane = threadIdx.x & 31;
+// ---- small dense linear algebra on the projected pencil -----------------------------
+// FP64 issues at a small fraction of the FP32 rate on this part, so these kernels keep
+// dependent chains short (one reciprocal square root per pivot, products with reciprocals
+// instead of divisions) and spread the O(m^2) work of each step over the whole block.
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+// Cholesky of a symmetric positive definite m x m matrix held in shared memory (row stride
+// ld), by the whole block.  Strict lower factor in place; the pivots as L_kk in dL (if set)
+// and 1 / L_kk in dinv.  Returns false (for every thread) if a pivot is not positive.
+__device__ bool blk_cholesky(double *G, int ld, int m, double *dinv, double *dL) {
+  const int nt = blockDim.x;
   for (int k = 0; k < m; ++k) {
-    double akk = G[k * ld + k];
+    const double akk = G[k * ld + k];
     if (!(akk > 0.0)) return false;
-    double lkk = sqrt(akk);
-    if (lane == 0) dL[k] = lkk;
-    for (int i = k + 1 + lane; i < m; i += 32) G[i * ld + k] /= lkk;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < m; i += 32) {
-      double lik = G[i * ld + k];
-      for (int j = k + 1; j <= i; ++j) G[i * ld + j] -= lik * G[j * ld + k];
+    const double r = rsqrt(akk);
+    for (int i = k + 1 + threadIdx.x; i < m; i += nt) G[i * ld + k] *= r;
+    if (threadIdx.x == 0) {
+      dinv[k] = r;
+      if (dL) dL[k] = akk * r;
     }
-    __syncwarp();
+    __syncthreads();
+    // trailing update of the lower triangle, element e -> (row k+1+ii, column k+1+jj), jj <= ii
+    const int n = m - k - 1, cnt = n * (n + 1) / 2;
+    for (int e = threadIdx.x; e < cnt; e += nt) {
+      int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int jj = e - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
+    }
+    __syncthreads();
   }
   return true;
 }
-// solve L L^T x = c in place (warp 0), L from warp_cholesky
-__device__ void warp_chol_solve(const double *G, int ld, int m, const double *dL, double *c) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < m; ++k) {
-    double yk = c[k] / dL[k];
-    __syncwarp();
-    if (lane == 0) c[k] = yk;
-    for (int i = k + 1 + lane; i < m; i += 32) c[i] -= G[i * ld + k] * yk;
-    __syncwarp();
-  }
-  for (int k = m - 1; k >= 0; --k) {
-    double xk = c[k] / dL[k];
-    __syncwarp();
-    if (lane == 0) c[k] = xk;
-    for (int i = lane; i < k; i += 32) c[i] -= G[k * ld + i] * xk;
-    __syncwarp();
-  }
-}
 
-// Rayleigh-Ritz setup: Hm = L L^T, Cw = L^-1 Hs L^-T.  L written to Lout (m x m, row-major).
-__global__ void __launch_bounds__(256) k_chol_rr(const double *__restrict__ Hm,
-                                                 const double *__restrict__ Hs, int m,
-                                                 double *__restrict__ Lout, double *__restrict__ Y,
-                                                 double *__restrict__ Cw, int *__restrict__ status) {
+// Rayleigh-Ritz setup, step 1: Hm = L L^T (one block).  L to Lout (m x m, row-major, zero
+// above the diagonal), 1 / L_ii to dinv_out.
+__global__ void __launch_bounds__(256) k_chol_rr(const double *__restrict__ Hm, int m,
+                                                 double *__restrict__ Lout, double *__restrict__ dinv_out,
+                                                 int *__restrict__ status) {
   extern __shared__ double sm[];
   const int ld = m + 1;
   double *G = sm;
   double *dL = G + m * ld;
-  __shared__ int ok_s;
+  double *dinv = dL + m;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     int i = idx / m, k = idx % m;
     G[i * ld + k] = 0.5 * (Hm[i * m + k] + Hm[k * m + i]);
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    bool ok = warp_cholesky(G, ld, m, dL);
-    if (threadIdx.x == 0) ok_s = ok ? 1 : 0;
-  }
-  __syncthreads();
-  if (!ok_s) {
+  if (!blk_cholesky(G, ld, m, dinv, dL)) {
     if (threadIdx.x == 0) *status = 1;
     return;
   }
@@ -502,27 +495,34 @@ __global__ void __launch_bounds__(256) k_chol_rr(const double *__restrict__ Hm,
     int i = idx / m, k = idx % m;
     Lout[idx] = (k < i) ? G[i * ld + k] : (k == i ? dL[i] : 0.0);
   }
-  // Y = L^-1 Hs, column by column (one thread per column)
-  for (int col = threadIdx.x; col < m; col += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      double acc = 0.5 * (Hs[i * m + col] + Hs[col * m + i]);
-      for (int k = 0; k < i; ++k) acc -= G[i * ld + k] * Y[k * m + col];
-      Y[i * m + col] = acc / dL[i];
-    }
-  }
-  __syncthreads();
-  // Cw^T = L^-1 Y^T: row r of Cw solves L z = (row r of Y)
-  for (int r = threadIdx.x; r < m; r += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      double acc = Y[r * m + i];
-      for (int k = 0; k < i; ++k) acc -= G[i * ld + k] * Cw[r * m + k];
-      Cw[r * m + i] = acc / dL[i];
-    }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) dinv_out[i] = dinv[i];
+}
+// Rayleigh-Ritz setup, steps 2 and 3 (Cw = L^-1 Hs L^-T), one warp per right-hand side:
+//   rows == 0: Y[:, j] = L^-1 sym(Hs)[:, j]      rows == 1: Cw[j, :] = L^-1 Y[j, :]
+// Forward substitution column by column of L (its column i read with stride m), the running
+// right-hand side in shared memory.  Skipped when the factorisation failed.
+__global__ void __launch_bounds__(128) k_rr_trsm(const double *__restrict__ R, const double *__restrict__ Lm,
+                                                 const double *__restrict__ dinv, int m, int rows,
+                                                 double *__restrict__ Out, const int *__restrict__ status) {
+  __shared__ double acc[4][MAXM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 4 + warp;
+  if (j >= m || *status) return;
+  double *a = acc[warp];
+  for (int i = lane; i < m; i += 32) a[i] = rows ? R[j * m + i] : 0.5 * (R[i * m + j] + R[j * m + i]);
+  __syncwarp();
+  for (int i = 0; i < m; ++i) {
+    const double yi = a[i] * dinv[i];
+    for (int k = i + 1 + lane; k < m; k += 32) a[k] -= Lm[k * m + i] * yi;
+    if (lane == 0) Out[rows ? j * m + i : i * m + j] = yi;
+    __syncwarp();
   }
 }
 
 // E = L^-T W (generalised eigenvectors, E^T Hm E = 1), theta = 1/mu, the ncol columns with
-// theta nearest the shift (ascending distance), each scaled to unit Euclidean norm.
+// theta nearest the shift (ascending distance), each scaled to unit Euclidean norm.  Only
+// the selected columns are back-substituted, one warp each; the running sums of L^T e = w
+// are held in shared memory and updated column by column (row i of L is contiguous).
 __global__ void __launch_bounds__(128) k_rr_select(const double *__restrict__ Lm,
                                                    const double *__restrict__ mu,
                                                    const double *__restrict__ W, int m,
@@ -532,20 +532,16 @@ __global__ void __launch_bounds__(128) k_rr_select(const double *__restrict__ Lm
                                                    double *__restrict__ Eout) {
   __shared__ int order[MAXM];
   __shared__ double dist[MAXM];
-  // back substitution per eigenvector j: L^T e = w
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const double *w = W + (long long)j * m;
-    double *e = Ework + (long long)j * m;
-    for (int i = m - 1; i >= 0; --i) {
-      double acc = w[i];
-      for (int k = i + 1; k < m; ++k) acc -= Lm[k * m + i] * e[k];
-      e[i] = acc / Lm[i * m + i];
-    }
-    double th = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
+  __shared__ double dinv[MAXM];
+  __shared__ double acc[4][MAXM];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = tid; j < m; j += blockDim.x) {
+    const double th = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
     dist[j] = fabs(th - shift);
+    dinv[j] = 1.0 / Lm[j * m + j];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     for (int j = 0; j < m; ++j) order[j] = j;
     for (int i = 0; i < ncol && i < m; ++i) {
       int best = i;
@@ -557,31 +553,31 @@ __global__ void __launch_bounds__(128) k_rr_select(const double *__restrict__ Lm
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
-    int j = order[t];
-    const double *e = Ework + (long long)j * m;
+  double *a = acc[warp];
+  for (int t = warp; t < ncol && t < m; t += 4) {
+    const int j = order[t];
+    const double *w = W + (long long)j * m;
+    double *e = Ework + (long long)t * m;
+    for (int i = lane; i < m; i += 32) a[i] = w[i];
+    __syncwarp();
+    // L^T e = w from the last row up: e_i = a_i / L_ii, then a_k -= L_ik e_i for k < i
+    for (int i = m - 1; i >= 0; --i) {
+      const double ei = a[i] * dinv[i];
+      for (int k = lane; k < i; k += 32) a[k] -= Lm[i * m + k] * ei;
+      if (lane == 0) e[i] = ei;
+      __syncwarp();
+    }
     double nrm = 0.0;
-    for (int i = 0; i < m; ++i) nrm += e[i] * e[i];
-    nrm = 1.0 / sqrt(nrm);
-    for (int i = 0; i < m; ++i) Eout[(long long)t * m + i] = e[i] * nrm;
-    theta_out[t] = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
+    for (int i = lane; i < m; i += 32) nrm += e[i] * e[i];
+    nrm = rsqrt(warp_sum(nrm));
+    for (int i = lane; i < m; i += 32) Eout[(long long)t * m + i] = e[i] * nrm;
+    if (lane == 0) theta_out[t] = (fabs(mu[j]) > 1e-300) ? 1.0 / mu[j] : 1e300;
+    __syncwarp();
   }
 }
 
-__device__ double blk_sum(double x, double *red) {
-  red[threadIdx.x] = x;
-  __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-    __syncthreads();
-  }
-  double r = red[0];
-  __syncthreads();
-  return r;
-}
-
-// Folded-spectrum vectors with deflation, one warp (the reduced problem has m <= 32).  For
-// target j:
+// Folded-spectrum vectors with deflation, one block of four warps (the reduced problem has
+// m <= 32).  For target j:
 //   w <- th0[j]; repeat reps times:
 //     G(w) = (MV - w SV)^T (MV - w SV) = Gmm - w (Gms + Gms^T) + w^2 Gss,
 //     restricted to coefficients Euclidean-orthogonal to Hs c_i (i < j): P G(w) P + gamma Q^T Q
@@ -591,28 +587,66 @@ __device__ double blk_sum(double x, double *red) {
 // direction q (orthogonal to the earlier ones) updates them by a rank-2 term,
 //   A <- A - (A q) q^T - q (A q)^T + (q^T A q) q q^T,
 // so a repetition costs O(m^2) plus one Cholesky factorisation.
-__device__ __forceinline__ double warp_sum(double x) {
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+//
+// FP64 runs at a small fraction of the FP32 rate on this part, so the kernel keeps the
+// dependent chains short: each Cholesky pivot takes one reciprocal square root, the
+// triangular solves multiply by those reciprocals with the right-hand side held in the
+// registers of warp 0 (element i in lane i), and the O(m^2) updates (trailing Cholesky
+// update, shifted matrix, rank-2 projections, matrix-vector products) are spread over all
+// four warps, so that all four schedulers of the SM issue FP64 work.
+constexpr int RT = 128;  // threads of k_refined
+// sum over the block of RT threads (every thread gets the result)
+__device__ double rt_sum(double x, double *red) {
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  const double r = red[0] + red[1] + red[2] + red[3];
+  __syncthreads();
+  return r;
 }
-__device__ void warp_rank2_project(double *A, int ld, int m, const double *q, double *u) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < m; i += 32) {
+// y = A x for m <= 32 (A row-major with leading dimension ld): thread (lane i, warp w) sums
+// the columns k = w mod 4; part holds 4 x 32 partial sums
+__device__ void rt_matvec(const double *A, int ld, int m, const double *x, double *y, double *part) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane < m) {
     double s = 0.0;
-    for (int k = 0; k < m; ++k) s += A[i * ld + k] * q[k];
-    u[i] = s;
+    for (int k = w; k < m; k += 4) s += A[lane * ld + k] * x[k];
+    part[w * 32 + lane] = s;
   }
-  __syncwarp();
-  double a = 0.0;
-  for (int i = lane; i < m; i += 32) a += q[i] * u[i];
-  a = warp_sum(a);
-  for (int idx = lane; idx < m * m; idx += 32) {
+  __syncthreads();
+  if (threadIdx.x < m) {
+    const int i = threadIdx.x;
+    y[i] = (part[i] + part[32 + i]) + (part[64 + i] + part[96 + i]);
+  }
+  __syncthreads();
+}
+// warp 0: solve L L^T x = y for the vector held one element per lane (lanes >= m hold 0)
+__device__ double warp_chol_solve_reg(const double *G, int ld, int m, const double *dinv, double y) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < m; ++k) {
+    const double yk = __shfl_sync(0xffffffffu, y, k) * dinv[k];
+    if (lane == k) y = yk;
+    else if (lane > k && lane < m) y -= G[lane * ld + k] * yk;
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const double xk = __shfl_sync(0xffffffffu, y, k) * dinv[k];
+    if (lane == k) y = xk;
+    else if (lane < k) y -= G[k * ld + lane] * xk;
+  }
+  return y;
+}
+// A <- A - u q^T - q u^T + (q^T u) q q^T with u = A q (u, part: scratch)
+__device__ void rt_rank2_project(double *A, int ld, int m, const double *q, double *u, double *part,
+                                 double *red) {
+  rt_matvec(A, ld, m, q, u, part);
+  const double a = rt_sum(threadIdx.x < m ? q[threadIdx.x] * u[threadIdx.x] : 0.0, red);
+  for (int idx = threadIdx.x; idx < m * m; idx += RT) {
     const int i = idx / m, k = idx % m;
     A[i * ld + k] += -u[i] * q[k] - q[i] * u[k] + a * q[i] * q[k];
   }
-  __syncwarp();
+  __syncthreads();
 }
-__global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
+__global__ void __launch_bounds__(RT) k_refined(const double *__restrict__ Hm,
                                                 const double *__restrict__ Hs,
                                                 const double *__restrict__ Gmm,
                                                 const double *__restrict__ Gms,
@@ -631,148 +665,139 @@ __global__ void __launch_bounds__(32) k_refined(const double *__restrict__ Hm,
   double *F = QQ + m * ld;      // the shifted matrix, then its Cholesky factor
   double *Qc = F + m * ld;      // b x m, orthonormal constraint directions
   double *c = Qc + b * m;       // m
-  double *t1 = c + m;           // m
-  double *dL = t1 + m;          // m
-  const int lane = threadIdx.x;
-  for (int idx = lane; idx < m * m; idx += 32) {
+  double *u = c + m;            // m
+  double *dinv = u + m;         // m
+  double *part = dinv + m;      // 4 x 32
+  double *red = part + 128;     // 8
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < m * m; idx += RT) {
     const int i = idx / m, k = idx % m;
     Amm[i * ld + k] = 0.5 * (Gmm[i * m + k] + Gmm[k * m + i]);
     Ams[i * ld + k] = Gms[i * m + k] + Gms[k * m + i];
     Ass[i * ld + k] = 0.5 * (Gss[i * m + k] + Gss[k * m + i]);
     QQ[i * ld + k] = 0.0;
   }
-  __syncwarp();
+  __syncthreads();
   for (int j = 0; j < b; ++j) {
     double w = th0[j];
-    for (int i = lane; i < m; i += 32) c[i] = C0[(long long)j * m + i];
-    __syncwarp();
+    if (tid < m) c[tid] = C0[(long long)j * m + tid];
+    __syncthreads();
     bool ok = true;
     for (int rep = 0; rep < reps && ok; ++rep) {
-      double tr = 0.0;
-      for (int i = lane; i < m; i += 32) tr += Amm[i * ld + i] - w * Ams[i * ld + i] + w * w * Ass[i * ld + i];
-      tr = fabs(warp_sum(tr));
+      const double tr = fabs(rt_sum(
+          tid < m ? Amm[tid * ld + tid] - w * Ams[tid * ld + tid] + w * w * Ass[tid * ld + tid] : 0.0, red));
       const double gamma = 10.0 * tr + 1e-300, delta = 1e-14 * tr + 1e-300;
-      for (int idx = lane; idx < m * m; idx += 32) {
+      for (int idx = tid; idx < m * m; idx += RT) {
         const int i = idx / m, k = idx % m;
         F[i * ld + k] = Amm[i * ld + k] - w * Ams[i * ld + k] + w * w * Ass[i * ld + k] + gamma * QQ[i * ld + k] +
                         (i == k ? delta : 0.0);
       }
-      __syncwarp();
-      ok = warp_cholesky(F, ld, m, dL);
+      __syncthreads();
+      ok = blk_cholesky(F, ld, m, dinv, nullptr);
       if (!ok) {
-        if (lane == 0) *status = 2;
+        if (tid == 0) *status = 2;
         break;
       }
-      for (int itv = 0; itv < 4; ++itv) {
-        // project c off the constraint directions (Q is orthonormal) and normalise
-        for (int p = 0; p < j; ++p) {
-          double sp = 0.0;
-          for (int i = lane; i < m; i += 32) sp += Qc[p * m + i] * c[i];
-          sp = warp_sum(sp);
-          if (lane == 0) t1[p] = sp;
+      if (warp == 0) {
+        double ci = lane < m ? c[lane] : 0.0;
+        for (int itv = 0; itv < 4; ++itv) {
+          // project c off the constraint directions (Q is orthonormal) and normalise
+          double proj = 0.0;
+          for (int p = 0; p < j; ++p) {
+            const double qp = lane < m ? Qc[p * m + lane] : 0.0;
+            proj += warp_sum(qp * ci) * qp;
+          }
+          ci -= proj;
+          double nn = warp_sum(ci * ci);
+          if (!(nn > 0.0)) nn = 1.0;
+          ci *= rsqrt(nn);
+          if (itv == 3) break;
+          ci = warp_chol_solve_reg(F, ld, m, dinv, ci);
         }
-        __syncwarp();
-        for (int i = lane; i < m; i += 32) {
-          double ci = c[i];
-          for (int p = 0; p < j; ++p) ci -= t1[p] * Qc[p * m + i];
-          c[i] = ci;
-        }
-        __syncwarp();
-        double nn = 0.0;
-        for (int i = lane; i < m; i += 32) nn += c[i] * c[i];
-        nn = warp_sum(nn);
-        if (!(nn > 0.0)) nn = 1.0;
-        const double inv = 1.0 / sqrt(nn);
-        for (int i = lane; i < m; i += 32) c[i] *= inv;
-        __syncwarp();
-        if (itv == 3) break;
-        warp_chol_solve(F, ld, m, dL, c);
-        __syncwarp();
+        if (lane < m) c[lane] = ci;
       }
+      __syncthreads();
       // fold centre follows the Rayleigh quotient of the folded vector
-      double nm = 0.0, ns = 0.0;
-      for (int i = lane; i < m; i += 32) {
-        double hm = 0.0, hs = 0.0;
-        for (int k = 0; k < m; ++k) {
-          hm += Hm[i * m + k] * c[k];
-          hs += Hs[i * m + k] * c[k];
-        }
-        nm += c[i] * hm;
-        ns += c[i] * hs;
-      }
-      nm = warp_sum(nm);
-      ns = warp_sum(ns);
+      rt_matvec(Hm, m, m, c, u, part);
+      const double nm = rt_sum(tid < m ? c[tid] * u[tid] : 0.0, red);
+      rt_matvec(Hs, m, m, c, u, part);
+      const double ns = rt_sum(tid < m ? c[tid] * u[tid] : 0.0, red);
       if (fabs(ns) > 1e-300) w = nm / ns;
     }
-    for (int i = lane; i < m; i += 32) Cout[(long long)j * m + i] = c[i];
-    if (lane == 0) thout[j] = w;
+    if (tid < m) Cout[(long long)j * m + tid] = c[tid];
+    if (tid == 0) thout[j] = w;
     if (j + 1 == b) break;
     // new constraint direction: Hs c, orthonormalised against the previous ones (twice)
-    for (int i = lane; i < m; i += 32) {
-      double sacc = 0.0;
-      for (int k = 0; k < m; ++k) sacc += Hs[i * m + k] * c[k];
-      t1[i] = sacc;
+    rt_matvec(Hs, m, m, c, u, part);
+    if (warp == 0) {
+      double t = lane < m ? u[lane] : 0.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int p = 0; p < j; ++p) {
+          const double qp = lane < m ? Qc[p * m + lane] : 0.0;
+          t -= warp_sum(qp * t) * qp;
+        }
+      const double nn = warp_sum(t * t);
+      const double inv = (nn > 1e-300) ? rsqrt(nn) : 0.0;
+      if (lane < m) Qc[j * m + lane] = t * inv;
     }
-    __syncwarp();
-    for (int pass = 0; pass < 2; ++pass)
-      for (int p = 0; p < j; ++p) {
-        double sp = 0.0;
-        for (int i = lane; i < m; i += 32) sp += Qc[p * m + i] * t1[i];
-        sp = warp_sum(sp);
-        for (int i = lane; i < m; i += 32) t1[i] -= sp * Qc[p * m + i];
-        __syncwarp();
-      }
-    double nn = 0.0;
-    for (int i = lane; i < m; i += 32) nn += t1[i] * t1[i];
-    nn = warp_sum(nn);
-    double inv = (nn > 1e-300) ? 1.0 / sqrt(nn) : 0.0;
-    for (int i = lane; i < m; i += 32) Qc[j * m + i] = t1[i] * inv;
-    __syncwarp();
-    // fold it into the projected Grams and Q^T Q (the Cholesky buffer F is free as scratch)
+    __syncthreads();
+    // fold it into the projected Grams and Q^T Q
     const double *q = Qc + j * m;
-    warp_rank2_project(Amm, ld, m, q, F);
-    warp_rank2_project(Ams, ld, m, q, F);
-    warp_rank2_project(Ass, ld, m, q, F);
-    for (int idx = lane; idx < m * m; idx += 32) {
+    rt_rank2_project(Amm, ld, m, q, u, part, red);
+    rt_rank2_project(Ams, ld, m, q, u, part, red);
+    rt_rank2_project(Ass, ld, m, q, u, part, red);
+    for (int idx = tid; idx < m * m; idx += RT) {
       const int i = idx / m, k = idx % m;
       QQ[i * ld + k] += q[i] * q[k];
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
-// modified Gram-Schmidt of ncol coefficient vectors K[t][m] (Euclidean); the first nout
-// independent ones go to Q[t][m]; *nkept receives their count.
-__global__ void __launch_bounds__(128) k_mgs(const double *__restrict__ K, int m, int ncol, int nout,
-                                             double *__restrict__ Qo, int *__restrict__ nkept, double tol) {
-  __shared__ double red[128];
+// Gram-Schmidt (classical, applied twice) of ncol coefficient vectors K[t][m] (Euclidean);
+// the first nout (<= 64) independent ones go to Q[t][m]; *nkept receives their count.  One
+// block of RT threads: the projections of a pass are formed together, one warp per earlier
+// vector, and subtracted together.
+__global__ void __launch_bounds__(RT) k_mgs(const double *__restrict__ K, int m, int ncol, int nout,
+                                            double *__restrict__ Qo, int *__restrict__ nkept, double tol) {
+  __shared__ double red[8];
   __shared__ double v[MAXM];
+  __shared__ double sdot[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  nout = min(nout, 64);
   int kept = 0;
   for (int t = 0; t < ncol && kept < nout; ++t) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = K[(long long)t * m + i];
+    for (int i = tid; i < m; i += RT) v[i] = K[(long long)t * m + i];
     __syncthreads();
     double n0 = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) n0 += v[i] * v[i];
-    n0 = blk_sum(n0, red);
-    for (int pass = 0; pass < 2; ++pass)
-      for (int p = 0; p < kept; ++p) {
+    for (int i = tid; i < m; i += RT) n0 += v[i] * v[i];
+    n0 = rt_sum(n0, red);
+    for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+      for (int p = warp; p < kept; p += RT / 32) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) s += Qo[(long long)p * m + i] * v[i];
-        s = blk_sum(s, red);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] -= s * Qo[(long long)p * m + i];
-        __syncthreads();
+        for (int i = lane; i < m; i += 32) s += Qo[(long long)p * m + i] * v[i];
+        s = warp_sum(s);
+        if (lane == 0) sdot[p] = s;
       }
+      __syncthreads();
+      for (int i = tid; i < m; i += RT) {
+        double x = v[i];
+        for (int p = 0; p < kept; ++p) x -= sdot[p] * Qo[(long long)p * m + i];
+        v[i] = x;
+      }
+      __syncthreads();
+    }
     double n1 = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) n1 += v[i] * v[i];
-    n1 = blk_sum(n1, red);
+    for (int i = tid; i < m; i += RT) n1 += v[i] * v[i];
+    n1 = rt_sum(n1, red);
     if (n1 > tol * n0 && n1 > 0.0) {
-      double inv = 1.0 / sqrt(n1);
-      for (int i = threadIdx.x; i < m; i += blockDim.x) Qo[(long long)kept * m + i] = v[i] * inv;
+      const double inv = rsqrt(n1);
+      for (int i = tid; i < m; i += RT) Qo[(long long)kept * m + i] = v[i] * inv;
       ++kept;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *nkept = kept;
+  if (tid == 0) *nkept = kept;
 }
 
 // ---------------------------------------------------------------------------
@@ -834,6 +859,7 @@ struct Window {
   double *X = nullptr, *MX = nullptr, *SX = nullptr;  // [64][L]
   double *Vr = nullptr, *MVr = nullptr, *SVr = nullptr;  // [32][L] reduced blocks for the folded step
   double *Hm, *Hs, *Gmm, *Gms, *Gss, *Lm, *Yw, *Cw, *mu, *W, *Ew, *Esel, *thsel, *Cref, *thref, *Kc, *Qk;
+  double *dinv;  // 1 / L_ii of the Rayleigh-Ritz Cholesky factor
   double *Qr, *hm, *hs, *C0, *Cred;
   int *dstat, *dkept;
   std::vector<double> h_theta, h_res, h_xsx;
@@ -948,14 +974,14 @@ struct WindowBatch {
       wi.SVr = take(vecbytes * 32);
       double **mats[] = {&wi.Hm, &wi.Hs, &wi.Gmm, &wi.Gms, &wi.Gss, &wi.Lm, &wi.Yw, &wi.Cw, &wi.mu,
                          &wi.W, &wi.Ew, &wi.Esel, &wi.thsel, &wi.Cref, &wi.thref, &wi.Kc, &wi.Qk,
-                         &wi.Qr, &wi.hm, &wi.hs, &wi.C0, &wi.Cred};
+                         &wi.Qr, &wi.hm, &wi.hs, &wi.C0, &wi.Cred, &wi.dinv};
       for (double **q : mats) *q = take(sizeof(double) * mm);
       wi.dstat = (int *)take(sizeof(double) * mm);
       wi.dkept = wi.dstat + 4;
     }
     const int ld = MAXM + 1;
     const int smem_jac = 2 * MAXM * MAXM * (int)sizeof(double);
-    const int smem_chol = (MAXM * ld + MAXM) * (int)sizeof(double);
+    const int smem_chol = (MAXM * ld + 2 * MAXM) * (int)sizeof(double);
     const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
     PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
     PP_CUDA(cudaFuncSetAttribute(k_chol_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
@@ -1154,8 +1180,12 @@ struct WindowBatch {
     sv.gram(wi.V, L, m, wi.MV, L, m, wi.Hm, m);
     sv.gram(wi.V, L, m, wi.SV, L, m, wi.Hs, m);
     PP_CUDA(cudaMemsetAsync(wi.dstat, 0, sizeof(int) * 4, s));
-    k_chol_rr<<<1, 256, (m * (m + 1) + m) * sizeof(double), s>>>(wi.Hm, wi.Hs, m, wi.Lm, wi.Yw, wi.Cw, wi.dstat);
+    k_chol_rr<<<1, 256, (m * (m + 1) + 2 * m) * sizeof(double), s>>>(wi.Hm, m, wi.Lm, wi.dinv, wi.dstat);
     PP_LAUNCH_CHECK("k_chol_rr");
+    k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(wi.Hs, wi.Lm, wi.dinv, m, 0, wi.Yw, wi.dstat);
+    PP_LAUNCH_CHECK("k_rr_trsm");
+    k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(wi.Yw, wi.Lm, wi.dinv, m, 1, wi.Cw, wi.dstat);
+    PP_LAUNCH_CHECK("k_rr_trsm");
     int mp = (m + 1) & ~1;
     k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
     PP_LAUNCH_CHECK("k_jacobi_eig");
@@ -1165,7 +1195,7 @@ struct WindowBatch {
     // folded step in the span of the nr Rayleigh-Ritz vectors nearest the shift: orthonormal
     // coefficients Qr, reduced blocks V Qr^T, M V Qr^T, Sigma V Qr^T, and their small Grams
     const int nr = std::min(nsel, 32);
-    k_mgs<<<1, 128, 0, s>>>(wi.Esel, m, nsel, nr, wi.Qr, wi.dkept, 0.0);
+    k_mgs<<<1, RT, 0, s>>>(wi.Esel, m, nsel, nr, wi.Qr, wi.dkept, 0.0);
     PP_LAUNCH_CHECK("k_mgs");
     sv.combine(wi.V, m, wi.Qr, m, nr, wi.Vr, 1.0, 0.0);
     sv.combine(wi.MV, m, wi.Qr, m, nr, wi.MVr, 1.0, 0.0);
@@ -1183,7 +1213,7 @@ struct WindowBatch {
       g.C = wi.C0; g.c_m = nr; g.c_n = 1;
       gemm_f64(g, s);
     }
-    k_refined<<<1, 32, (5 * nr * (nr + 1) + b * nr + 3 * nr) * sizeof(double), s>>>(
+    k_refined<<<1, RT, (5 * nr * (nr + 1) + b * nr + 3 * nr + 136) * sizeof(double), s>>>(
         wi.hm, wi.hs, wi.Gmm, wi.Gms, wi.Gss, nr, b, 4, wi.thsel, wi.C0, wi.Cred, wi.thref, wi.dstat);
     PP_LAUNCH_CHECK("k_refined");
     sv.combine(wi.Vr, nr, wi.Cred, nr, b, wi.X, 1.0, 0.0);
@@ -1383,7 +1413,7 @@ struct WindowBatch {
     PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
                             cudaMemcpyDeviceToDevice, s));
     const int nout = std::min(64, std::min(m, 2 * b));
-    k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
+    k_mgs<<<1, RT, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
     PP_LAUNCH_CHECK("k_mgs");
     int kept = 0;
     PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1417,7 +1447,7 @@ struct WindowBatch {
       PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
       PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
                               cudaMemcpyDeviceToDevice, s));
-      k_mgs<<<1, 128, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept, 1e-20);
+      k_mgs<<<1, RT, 0, s>>>(wi.Kc, m, b + nsel, std::min(keep, 64), wi.Qk, wi.dkept, 1e-20);
       PP_LAUNCH_CHECK("k_mgs");
       int kept = 0;
       PP_CUDA(cudaMemcpyAsync(&kept, wi.dkept, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -543,14 +543,16 @@ __global__ void k_vT(const double *__restrict__ V, int R, int o, int v, long lon
     if (lo) lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
-// booR[i][(Q,k)] = Boo[Q][i][k] (zero up to ldk), Boo double [Q][o][o], as a BF16 pair
-__global__ void k_boo_r(const double *__restrict__ Boo, int Q, int o, long long ldk, __nv_bfloat16 *__restrict__ hi,
+// bvvK[a][Q v + b] = Bvv[Q][a][b] (zero up to ldk), Bvv double [Q][v][v], as a BF16 pair: the
+// operand of the exchange contraction sum_(Q,b) U_Q[i][b] Bvv_Q[b][a] (the same Bvv_Q element
+// the W = V Bvv_Q contraction reads)
+__global__ void k_bvv_k(const double *__restrict__ Bvv, int Q, int v, long long ldk, __nv_bfloat16 *__restrict__ hi,
                         __nv_bfloat16 *__restrict__ lo) {
-  const long long total = (long long)o * ldk;
+  const long long total = (long long)v * ldk;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
-    const long long i = p / ldk, qk = p % ldk;
-    const float x = (qk < (long long)Q * o) ? (float)Boo[((qk / o) * o + i) * o + qk % o] : 0.f;
+    const long long a = p / ldk, qb = p % ldk;
+    const float x = (qb < (long long)Q * v) ? (float)Bvv[((qb / v) * v + a) * v + qb % v] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     hi[p] = h;
     lo[p] = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -631,8 +633,14 @@ static CUtensorMap kmajor_map(const void *base, long long K, long long rows, lon
   return m;
 }
 
-constexpr int GEMM_BN = 256, GEMM_STAGES = 4, TGEN_STAGES = 3;
-constexpr size_t gemm_smem() { return (size_t)GEMM_STAGES * (BM * BK * 2 + GEMM_BN * BK * 2) + 1024; }
+// GEMM_STAGES for long reductions; GEMM_STAGES_SHORT (97 KB of shared memory) for GEMMs of a
+// few K steps, whose time goes to the epilogue: two CTAs then share an SM (their two 256-column
+// accumulators fill its TMEM), so one CTA's epilogue overlaps the other's main loop.
+constexpr int GEMM_BN = 256, GEMM_STAGES = 4, GEMM_STAGES_SHORT = 2, TGEN_STAGES = 3;
+constexpr int GEMM_SHORT_STEPS = 24;  // nseg * K / BK at or below which the short form is used
+constexpr size_t gemm_smem(int stages = GEMM_STAGES) {
+  return (size_t)stages * (BM * BK * 2 + GEMM_BN * BK * 2) + 1024;
+}
 constexpr size_t tgen_smem() { return (size_t)TGEN_STAGES * 4 * BM * BK * 2 + 1024; }
 
 // out (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K; output addressing per GemmOut
@@ -643,6 +651,8 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
   if (!attr) {
     PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gemm_smem()));
+    PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES_SHORT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(GEMM_STAGES_SHORT)));
     attr = true;
   }
   GemmMaps maps;
@@ -663,7 +673,10 @@ void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *
     grid.z = (unsigned)ks;
   }
   if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
-  k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
+  if (a.ksplit == 1 && (long long)nseg * a.nk <= GEMM_SHORT_STEPS)
+    k_gemm_bf16<GEMM_BN, GEMM_STAGES_SHORT><<<grid, 128, gemm_smem(GEMM_STAGES_SHORT), s>>>(maps, a);
+  else
+    k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
 }
 
@@ -711,9 +724,9 @@ struct TcPlan {
   DevBuf gam_hi, gam_lo;     // [(Q,i)][vp]        F = Gam_Q V^T
   DevBuf bvvT_hi, bvvT_lo;   // [a][(c,Qp)]        sum_Q P_Q Bvv_Q
   DevBuf booT_hi, booT_lo;   // [i][(k,Qp)]        sum_Q Boo_Q P_Q
-  long long kbo = 0, kqo = 0, kef = 0;  // padded K of the U, KA and KB contractions
+  long long kbo = 0, kqv = 0, kef = 0;  // padded K of the U, KA and KB contractions
   DevBuf booK_hi, booK_lo;   // [(Q,l)][kbo]       U = Boo_Q V
-  DevBuf booR_hi, booR_lo;   // [i][(Q,k)]         KA = sum_Q Boo_Q W_Q
+  DevBuf bvvK_hi, bvvK_lo;   // [a][(Q,b)]         KA = sum_(Q,b) U_Q Bvv_Q
   DevBuf gbT_hi, gbT_lo;     // [a][(t,j)]         KB = sum_t EF_t GB_t
   // FP32 copies of the operands of the remaining SIMT contractions
   DevBuf f_gap, f_eps, f_Bov, f_Boo, f_Bvv, f_BvvP, f_BooT, f_GB, f_Gam, f_poo, f_qoo, f_pvv, f_qvv;
@@ -726,7 +739,7 @@ struct TcPlan {
   DevBuf p2_hi, p2_lo;       // P as [(r,a)][(k,Qp)]
   DevBuf vT_hi, vT_lo;       // V^T [(r,b)][kbo]
   DevBuf uC;                 // U = Boo_Q V (FP32) in the layout of C_Q(V)
-  DevBuf kaB_hi, kaB_lo;     // W as [(r,a)][(Q,k)]
+  DevBuf kaU_hi, kaU_lo;     // U as [(r,i)][(Q,b)]
   DevBuf efB_hi, efB_lo;     // E, F as [(r,i)][(t,j)]
   DevBuf err;
 };
@@ -740,8 +753,8 @@ size_t tc_plan_bytes(const pp_ctx *c) {
                           &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                           &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                           &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
-                          &p->booR_hi, &p->booR_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
-                          &p->kaB_hi, &p->kaB_lo, &p->efB_hi, &p->efB_lo};
+                          &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                          &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
   size_t n = 0;
   for (const DevBuf *b : bufs) n += b->bytes;
   return n;
@@ -756,8 +769,8 @@ void tc_destroy(pp_ctx *c) {
                     &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                     &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                     &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
-                    &p->booR_hi, &p->booR_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
-                    &p->kaB_hi, &p->kaB_lo, &p->efB_hi, &p->efB_lo};
+                    &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                    &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
   for (DevBuf *b : bufs) b->release();
   for (auto &v : p->prof.ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -837,19 +850,18 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   f32_copy(p->f_BvvP, c->BvvP, Q * v * v, s);
   f32_copy(p->f_BooT, c->BooT, Q * o * o, s);
   p->kbo = pad64(o);
-  p->kqo = pad64(Q * o);
+  p->kqv = pad64(Q * v);
   p->kef = pad64(2 * Q * o);
   if (c->opt.order >= 1 && Q > 0) {
     bf16_pair(p->bvv_hi, p->bvv_lo, c->Bvv.as<double>(), Q * v, v, v, p->vp, s);
     bf16_pair(p->bov_hi, p->bov_lo, c->Bov.as<double>(), Q * o, v, v, p->vp, s);
-    p->booR_hi.ensure(sizeof(__nv_bfloat16) * (size_t)o * p->kqo);
-    p->booR_lo.ensure(sizeof(__nv_bfloat16) * (size_t)o * p->kqo);
-    tc::k_boo_r<<<tc::grid_for(o * p->kqo), 256, 0, s>>>(c->Boo.as<double>(), (int)Q, (int)o, p->kqo,
-                                                         p->booR_hi.as<__nv_bfloat16>(), p->booR_lo.as<__nv_bfloat16>());
-    PP_LAUNCH_CHECK("k_boo_r");
-  }
-  if (c->opt.order >= 2 && Q > 0)
+    p->bvvK_hi.ensure(sizeof(__nv_bfloat16) * (size_t)v * p->kqv);
+    p->bvvK_lo.ensure(sizeof(__nv_bfloat16) * (size_t)v * p->kqv);
+    tc::k_bvv_k<<<tc::grid_for(v * p->kqv), 256, 0, s>>>(c->Bvv.as<double>(), (int)Q, (int)v, p->kqv,
+                                                         p->bvvK_hi.as<__nv_bfloat16>(), p->bvvK_lo.as<__nv_bfloat16>());
+    PP_LAUNCH_CHECK("k_bvv_k");
     bf16_pair(p->booK_hi, p->booK_lo, c->Boo.as<double>(), Q * o, o, o, p->kbo, s);
+  }
   if (c->opt.order >= 2 && Q > 0) {
     p->bovT_hi.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
     p->bovT_lo.ensure(sizeof(__nv_bfloat16) * (size_t)ov * p->ldq);
@@ -872,7 +884,7 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   }
   // chunk of R half-vectors: FP32 W, U, E/F plus BF16 C_Q(V) and two BF16 copies of P
   const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 2 * 2 * Q * p->ldT +
-                             2 * 2 * 2 * ov * p->Qp;
+                             2 * 2 * 2 * ov * p->Qp + 2 * 2 * o * p->kqv;
   long long R = tc_workspace_bytes(c) / std::max<long long>(per_half, 1);
   R = std::max<long long>(2, std::min<long long>(R, 64));
   R &= ~1LL;
@@ -1027,14 +1039,14 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     p->v_hi.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
     p->v_lo.ensure(sizeof(bf) * (size_t)Rmax * o * vp);
     // K paddings (and, at first order, the F half of EF) stay zero: never written
-    ensure_zeroed(p->kaB_hi, sizeof(bf) * (size_t)Rmax * v * p->kqo, s);
-    ensure_zeroed(p->kaB_lo, sizeof(bf) * (size_t)Rmax * v * p->kqo, s);
+    ensure_zeroed(p->kaU_hi, sizeof(bf) * (size_t)Rmax * o * p->kqv, s);
+    ensure_zeroed(p->kaU_lo, sizeof(bf) * (size_t)Rmax * o * p->kqv, s);
+    p->vT_hi.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
+    p->vT_lo.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
     ensure_zeroed(p->efB_hi, sizeof(bf) * (size_t)Rmax * o * p->kef, s);
     ensure_zeroed(p->efB_lo, sizeof(bf) * (size_t)Rmax * o * p->kef, s);
   }
   if (c->opt.order >= 2) {
-    p->vT_hi.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
-    p->vT_lo.ensure(sizeof(bf) * (size_t)Rmax * v * p->kbo);
     p->uC.ensure(sizeof(float) * (size_t)Rmax * Q * ldT);
     ensure_zeroed(p->c_hi, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
     ensure_zeroed(p->c_lo, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
@@ -1079,70 +1091,70 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     hk.first_order = [&](int Rc, float *Aacc, float *Bacc) {
       const int nseg1 = 3;
       const int order = c->opt.order;
-      const long long kbo = p->kbo, kqo = p->kqo, kef = p->kef;
-      bf *kah = p->kaB_hi.as<bf>(), *kal = p->kaB_lo.as<bf>();
+      const long long kbo = p->kbo, kqv = p->kqv, kef = p->kef;
+      bf *kuh = p->kaU_hi.as<bf>(), *kul = p->kaU_lo.as<bf>();
       bf *efh = p->efB_hi.as<bf>(), *efl = p->efB_lo.as<bf>();
       const bf *A[3], *B[3];
-      if (order >= 2) {
-        // U[r][Q][l][b] = sum_k Boo[Q][l][k] V[r][k][b]: rows (Q,l), columns (r,b), K = k; FP32 in
-        // the layout of C_Q(V), [(r,Q)][(l,b)] with row stride ldT
+      // U[r][Q][l][b] = sum_k Boo[Q][l][k] V[r][k][b]: rows (Q,l), columns (r,b), K = k.  Written
+      // as the BF16 pair [(r,l)][(Q,b)] (row stride kqv), the K-major operand of KA, and at
+      // second order also in FP32 in the layout of C_Q(V), [(r,Q)][(l,b)] with row stride ldT.
+      // Both layouts keep b contiguous, so each output row goes out in 16-byte stores.
+      {
         tc::k_vT<<<tc::grid_for((long long)Rc * v * kbo), 256, 0, s>>>(V64, Rc, o, v, kbo, p->vT_hi.as<bf>(),
                                                                       p->vT_lo.as<bf>());
         PP_LAUNCH_CHECK("k_vT");
         seg3(p->booK_hi.as<bf>(), p->booK_lo.as<bf>(), p->vT_hi.as<bf>(), p->vT_lo.as<bf>(), A, B);
-        tc::GemmOut u;
-        u.C = p->uC.as<float>();
-        u.d_r = o;
-        u.s_r1 = ldT;
-        u.s_r0 = v;
-        u.d_c = v;
-        u.s_c1 = (long long)Q * ldT;
-        u.s_c0 = 1;
-        tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, u, err, s);
-      }
-      // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d).  Written as
-      // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction and as
-      // [(r,a)][(Q,k)] for KA
-      {
-        seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
-        tc::GemmOut ka;
-        ka.Chi = kah;
-        ka.Clo = kal;
-        ka.d_r = o;
-        ka.s_r1 = (long long)v * kqo;
-        ka.s_r0 = 1;
-        ka.d_c = v;
-        ka.s_c1 = o;
-        ka.s_c0 = kqo;
+        tc::GemmOut ku;
+        ku.Chi = kuh;
+        ku.Clo = kul;
+        ku.d_r = o;
+        ku.s_r1 = v;
+        ku.s_r0 = kqv;
+        ku.d_c = v;
+        ku.s_c1 = (long long)o * kqv;
+        ku.s_c0 = 1;
         if (order >= 2) {
-          tc::GemmOut cc;
-          cc.Chi = p->c_hi.as<bf>();
-          cc.Clo = split ? p->c_lo.as<bf>() : nullptr;
-          cc.d_r = o;
-          cc.s_r1 = (long long)Q * ldT;
-          cc.s_r0 = v;
-          cc.d_c = v;
-          cc.s_c1 = ldT;
-          cc.s_c0 = 1;
-          cc.add = p->uC.as<float>();
-          cc.add_scale = -1.f;
-          tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s, &ka);
+          tc::GemmOut u;
+          u.C = p->uC.as<float>();
+          u.d_r = o;
+          u.s_r1 = ldT;
+          u.s_r0 = v;
+          u.d_c = v;
+          u.s_c1 = (long long)Q * ldT;
+          u.s_c0 = 1;
+          tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, u, err, s, &ku);
         } else {
-          tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, ka, err, s);
+          tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, ku, err, s);
         }
       }
-      // KA: Aacc[r][i][a] -= sum_(Q,k) Boo[Q][i][k] W[r][k][Q][a]   (rows i, columns (r,a))
+      // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d), written as
+      // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction
+      if (order >= 2) {
+        seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
+        tc::GemmOut cc;
+        cc.Chi = p->c_hi.as<bf>();
+        cc.Clo = split ? p->c_lo.as<bf>() : nullptr;
+        cc.d_r = o;
+        cc.s_r1 = (long long)Q * ldT;
+        cc.s_r0 = v;
+        cc.d_c = v;
+        cc.s_c1 = ldT;
+        cc.s_c0 = 1;
+        cc.add = p->uC.as<float>();
+        cc.add_scale = -1.f;
+        tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s);
+      }
+      // KA: Aacc[r][i][a] -= sum_(Q,k) Boo[Q][i][k] W[r][k][Q][a] = sum_(Q,b) U[r][Q][i][b] Bvv[Q][b][a]
+      // (rows (r,i), columns a, K = (Q,b))
       {
-        seg3(p->booR_hi.as<bf>(), p->booR_lo.as<bf>(), kah, kal, A, B);
+        seg3(kuh, kul, p->bvvK_hi.as<bf>(), p->bvvK_lo.as<bf>(), A, B);
         tc::GemmOut out;
         out.C = Aacc;
         out.s_r0 = v;
-        out.d_c = v;
-        out.s_c1 = ov;
         out.s_c0 = 1;
         out.alpha = -1.f;
         out.accumulate = 1;
-        tc::gemm_bf16(o, Rc * v, kqo, nseg1, A, kqo, B, kqo, out, err, s);
+        tc::gemm_bf16(Rc * o, v, kqv, nseg1, A, kqv, B, kqv, out, err, s);
       }
       // E and F: EF[(r,i)][(t,j)] = sum_b X_t[i][b] V[r][j][b], X = Bov (t < Q), Gamma (t >= Q)
       {
