@@ -144,6 +144,13 @@ def make_dot_inputs():
     return make_inputs(w["nocc"], w["nvir"], w["naux"], seed=w["seed"], mode=w["mode"])
 
 
+# DRAM bytes (read + write) of one slab-GEMM launch from an ncu capture of the bench dot
+# (profiles/k_gemm_bf16_dot-64x256x768_sigma8.md); the timed launches mix R and the split form,
+# so this is the traffic of the captured launch shape, next to its algorithmic minimum
+SLAB_GEMM_CAPTURE = dict(dram_bytes=880.2e6, algorithmic_bytes=570e6,
+                         launch="R = 16 half-vectors, BF16 phase: 2048 x 12288 x 16384 (8.25e11 FLOP)")
+
+
 def sigma_flops(o, v, Q, nvec):
     """Algorithmic FLOPs of one sigma batch (nvec supervectors, both halves)."""
     ov = o * v
@@ -259,9 +266,11 @@ def run_ours(args, world, rank, local):
 
     achieved = (k0["flops"] / (k0["ms"] / 1e3) / 1e12) if k0["ms"] > 0 else None
     peak = pk["bf16_sustained"]
+    cap = SLAB_GEMM_CAPTURE
     roof = dict(bound="tensor", kernel="k_gemm_bf16 (amplitude contraction, tcgen05)",
                 achieved=achieved, peak=peak, unit="TFLOP/s",
-                frac=(achieved / peak) if achieved else None, traffic=None,
+                frac=(achieved / peak) if achieved else None, traffic=cap["dram_bytes"],
+                traffic_launch=cap["launch"], traffic_algorithmic_bytes=cap["algorithmic_bytes"],
                 peak_source=f"{pk['src']} bf16 sustained", launches=k0["launches"],
                 avg_launch_ms=(k0["ms"] / k0["launches"]) if k0["launches"] else None,
                 tgen=dict(launches=k1["launches"], ms=k1["ms"],

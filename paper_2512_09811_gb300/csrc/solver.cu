@@ -78,81 +78,165 @@ __global__ void __launch_bounds__(256) k_gram(const double *__restrict__ A, long
     part[(long long)blockIdx.x * npair + pr] = acc[e];
   }
 }
-__global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int p, int q,
-                              double *__restrict__ G, int ldg, double alpha, double beta) {
-  int pr = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per output: the partials are summed lane-strided, then across the warp
+__global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ part, int nblk, int p, int q,
+                                                     double *__restrict__ G, int ldg, double alpha, double beta) {
+  const int lane = threadIdx.x & 31;
+  const int pr = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (pr >= p * q) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(long long)b * p * q + pr];
-  int i = pr / q, j = pr % q;
-  double *g = G + (long long)i * ldg + j;
-  *g = alpha * s + (beta != 0.0 ? beta * (*g) : 0.0);
+  for (int b = lane; b < nblk; b += 32) s += part[(long long)b * p * q + pr];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    int i = pr / q, j = pr % q;
+    double *g = G + (long long)i * ldg + j;
+    *g = alpha * s + (beta != 0.0 ? beta * (*g) : 0.0);
+  }
 }
 
-// ---- 2-D tiled Gram: part[chunk][i][j] = sum_{l in chunk} A_i[l] B_j[l], 32 x 32 pair tiles ---
+// ---- double-FP32 arithmetic for the Krylov-space products --------------------------------
+// FP64 issues at a small fraction of the FP32 rate on this part, and the Grams and linear
+// combinations of the basis are long FP64 dot products, so they run in double-FP32: each FP64
+// operand becomes an unevaluated sum hi + lo of two floats (48 significant bits), products are
+// formed with the exact FMA residual of hi * hi plus the two cross terms, and sums are kept as
+// float pairs with an error-free two-sum (relative error about 2^-46 of the sum of |terms|,
+// the level of FP64 summation over these lengths).  The operations of the two-sum carry
+// explicit rounding so that no step is contracted into an FMA.
+
+// hi = the leading 24 significant bits of x (truncated), lo = x - hi rounded to float; integer
+// operations only.  |x| < 2^-100 gives 0 (negligible next to the unit-scale entries here);
+// |x| > 2^100, inf and NaN take the plain conversion.
+__device__ __forceinline__ float2 split_df(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffULL) - 1023;
+  if (e < -100) return make_float2(0.f, 0.f);
+  if (e > 100) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  }
+  const unsigned long long mant = b & 0xfffffffffffffULL;
+  const float hi = __uint_as_float(sgn | ((unsigned int)(e + 127) << 23) | (unsigned int)(mant >> 29));
+  float lo = 0.f;
+  if (e >= -70) {
+    const float mag = __fmul_rn(__uint2float_rn((unsigned int)(mant & 0x1fffffffULL)),
+                                __uint_as_float((unsigned int)(e - 52 + 127) << 23));
+    lo = __uint_as_float(__float_as_uint(mag) | sgn);
+  }
+  return make_float2(hi, lo);
+}
+// (s, c) += a * b
+__device__ __forceinline__ void df_fma(float &s, float &c, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float w = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  c = __fadd_rn(c, __fadd_rn(w, e));
+  s = t;
+}
+
+// ---- 2-D tiled Gram: part[chunk][i][j] = sum_{l in chunk} A_i[l] B_j[l], 32 x 32 pair tiles,
+// 64 threads with 4 x 4 outputs each; double-FP32 products and sums, FP64 partials ---------
 constexpr int GT = 32, GRT = 32;
-__global__ void __launch_bounds__(256) k_gram2d(const double *__restrict__ A, long long lda, int p,
-                                                const double *__restrict__ B, long long ldb, int q,
-                                                long long L, long long chunk, int ntq,
-                                                double *__restrict__ part) {
-  __shared__ double As[GT][GRT + 1];
-  __shared__ double Bs[GT][GRT + 1];
+__global__ void __launch_bounds__(64) k_gram2d(const double *__restrict__ A, long long lda, int p,
+                                               const double *__restrict__ B, long long ldb, int q,
+                                               long long L, long long chunk, int ntq,
+                                               double *__restrict__ part) {
+  __shared__ float2 As[GRT][GT + 1];
+  __shared__ float2 Bs[GRT][GT + 1];
   const int ti = blockIdx.x / ntq, tj = blockIdx.x % ntq;
   const int i0 = ti * GT, j0 = tj * GT;
   const long long l0 = blockIdx.y * chunk, l1 = min(L, l0 + chunk);
   const int tid = threadIdx.x;
-  const int oi = tid >> 3, oj = (tid & 7) * 4;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int ty = tid >> 3, tx = tid & 7;
+  // warps whose rows or columns all fall outside the matrix skip the products
+  const bool active = (i0 + 4 * ty < p) && (j0 + 4 * tx < q);
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.f;
+  constexpr int NLD = GT * GRT / 64;  // elements of each operand tile per thread
   for (long long r0 = l0; r0 < l1; r0 += GRT) {
-    for (int idx = tid; idx < GT * GRT; idx += 256) {
-      int i = idx / GRT, rr = idx % GRT;
-      long long l = r0 + rr;
-      As[i][rr] = (i0 + i < p && l < l1) ? A[(long long)(i0 + i) * lda + l] : 0.0;
-      Bs[i][rr] = (j0 + i < q && l < l1) ? B[(long long)(j0 + i) * ldb + l] : 0.0;
+    // all loads of the tile issued before the first is used
+    double va[NLD], vb[NLD];
+#pragma unroll
+    for (int t = 0; t < NLD; ++t) {
+      const int idx = tid + 64 * t, i = idx / GRT, rr = idx % GRT;
+      const long long l = r0 + rr;
+      va[t] = (i0 + i < p && l < l1) ? A[(long long)(i0 + i) * lda + l] : 0.0;
+      vb[t] = (j0 + i < q && l < l1) ? B[(long long)(j0 + i) * ldb + l] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < NLD; ++t) {
+      const int idx = tid + 64 * t, i = idx / GRT, rr = idx % GRT;
+      As[rr][i] = split_df(va[t]);
+      Bs[rr][i] = split_df(vb[t]);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < GRT; ++rr) {
-      const double a = As[oi][rr];
+    if (active) {
+#pragma unroll 4
+      for (int rr = 0; rr < GRT; ++rr) {
+        float2 a[4], b[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) acc[t] = fma(a, Bs[oj + t][rr], acc[t]);
+        for (int t = 0; t < 4; ++t) {
+          a[t] = As[rr][4 * ty + t];
+          b[t] = Bs[rr][4 * tx + t];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) df_fma(s[x][y], c[x][y], a[x], b[y]);
+      }
     }
     __syncthreads();
   }
   const long long base = (long long)blockIdx.y * p * q;
-  for (int t = 0; t < 4; ++t) {
-    const int i = i0 + oi, j = j0 + oj + t;
-    if (i < p && j < q) part[base + (long long)i * q + j] = acc[t];
-  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = i0 + 4 * ty + x, j = j0 + 4 * tx + y;
+      if (i < p && j < q) part[base + (long long)i * q + j] = (double)s[x][y] + (double)c[x][y];
+    }
 }
 
 // ---- tall-skinny combine: Y[j][l] = alpha sum_k V[k][l] C[j][k] + beta Y[j][l], j < q ------
+// double-FP32 products and sums, as the Grams
 constexpr int CTS = 16;
 __global__ void __launch_bounds__(256) k_combine_ts(const double *__restrict__ V, long long ldv, int m,
                                                     const double *__restrict__ C, int ldc, int q,
                                                     double *__restrict__ Y, long long ldy, long long L,
                                                     double alpha, double beta) {
-  __shared__ double Cs[CTS][MAXM];
+  __shared__ float2 Cs[CTS][MAXM];
   const int j0 = blockIdx.y * CTS;
   const int nj = min(CTS, q - j0);
-  for (int idx = threadIdx.x; idx < nj * m; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < CTS * m; idx += blockDim.x) {
     int j = idx / m, k = idx % m;
-    Cs[j][k] = C[(long long)(j0 + j) * ldc + k];
+    Cs[j][k] = split_df(j < nj ? C[(long long)(j0 + j) * ldc + k] : 0.0);
   }
   __syncthreads();
   const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (l >= L) return;
-  double acc[CTS];
+  float s[CTS], c[CTS];
 #pragma unroll
-  for (int j = 0; j < CTS; ++j) acc[j] = 0.0;
+  for (int j = 0; j < CTS; ++j) s[j] = c[j] = 0.f;
+#pragma unroll 8
   for (int k = 0; k < m; ++k) {
-    const double vk = V[(long long)k * ldv + l];
+    const float2 vk = split_df(V[(long long)k * ldv + l]);
 #pragma unroll
-    for (int j = 0; j < CTS; ++j) acc[j] = fma(vk, Cs[j][k], acc[j]);
+    for (int j = 0; j < CTS; ++j) df_fma(s[j], c[j], vk, Cs[j][k]);
   }
-  for (int j = 0; j < nj; ++j) {
-    double *y = Y + (long long)(j0 + j) * ldy + l;
-    *y = alpha * acc[j] + (beta != 0.0 ? beta * (*y) : 0.0);
+#pragma unroll
+  for (int j = 0; j < CTS; ++j) {
+    if (j < nj) {
+      double *y = Y + (long long)(j0 + j) * ldy + l;
+      const double acc = (double)s[j] + (double)c[j];
+      *y = alpha * acc + (beta != 0.0 ? beta * (*y) : 0.0);
+    }
   }
 }
 
@@ -195,48 +279,82 @@ __global__ void k_cholqr(const double *__restrict__ Gin, int n, double tol, doub
 
 // ---- parallel cyclic Jacobi for a symmetric m x m matrix (m <= MAXM) -----------------
 // out: evals ascending in lam[m]; eigenvectors as rows E[j*m + i] (component i of vector j)
+//
+// A and the accumulated rotations V are held in double-FP32 (pairs hi + lo, 48 significant
+// bits) and rotated with double-FP32 products and sums: the FP64 rate of this part would
+// make the O(m^2) work of each of the m - 1 rounds of a sweep the dominant cost.  Rotation
+// angles are computed in FP32 from the pairs; the (c, s) of each rotation are then corrected
+// in double-FP32 so that c^2 + s^2 = 1 to about 2^-46, so every rotation stays orthogonal
+// whatever the accuracy of its angle (an angle off by 1e-7 relative leaves an off-diagonal
+// 1e-7 times smaller, removed by the next sweep).  The sweeps stop at an off-diagonal
+// Frobenius norm of 1e-11 relative, within reach of the pair precision.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = __fadd_rn(p, e);
+  return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float t = __fadd_rn(s, e);
+  return make_float2(t, __fsub_rn(e, __fsub_rn(t, s)));
+}
+// (c', s') = (c, s) (1 + eps) with (c^2 + s^2)(1 + eps)^2 = 1 to second order in the defect
+__device__ __forceinline__ void df_unit_rotation(float c, float s, float2 &cd, float2 &sd) {
+  const float c2 = __fmul_rn(c, c), c2e = fmaf(c, c, -c2);
+  const float s2 = __fmul_rn(s, s), s2e = fmaf(s, s, -s2);
+  // defect d = c^2 + s^2 - 1 (|d| ~ 1e-7): the high parts summed exactly, then the residuals
+  const float2 n = df_add(make_float2(c2, c2e), make_float2(s2, s2e));
+  const float d = __fadd_rn(__fsub_rn(n.x, 1.0f), n.y);
+  const float eps = fmaf(0.375f * d, d, -0.5f * d);
+  cd = make_float2(c, __fmul_rn(c, eps));
+  sd = make_float2(s, __fmul_rn(s, eps));
+}
 __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ Gin, int m,
                                                     double *__restrict__ lam,
                                                     double *__restrict__ E, int max_sweeps) {
-  extern __shared__ double sm[];
+  extern __shared__ double sm_raw[];
   const int mp = (m + 1) & ~1;
-  double *A = sm;            // mp x mp
-  double *V = sm + mp * mp;  // mp x mp, eigenvectors as columns
-  __shared__ double cs[MAXM / 2], sn[MAXM / 2];
+  float2 *A = reinterpret_cast<float2 *>(sm_raw);  // mp x mp
+  float2 *V = A + mp * mp;                          // mp x mp, eigenvectors as columns
+  __shared__ float2 cs[MAXM / 2], sn[MAXM / 2];
   __shared__ int pp[MAXM / 2], qq[MAXM / 2];
-  __shared__ double red[512];
+  __shared__ float red[512];
   __shared__ int perm[MAXM];
   const int tid = threadIdx.x, nt = blockDim.x;
-  double diag_big = 0.0;
   for (int idx = tid; idx < mp * mp; idx += nt) {
     int i = idx / mp, j = idx % mp;
     double a;
     if (i < m && j < m) a = 0.5 * (Gin[i * m + j] + Gin[j * m + i]);
     else a = 0.0;
-    A[idx] = a;
-    V[idx] = (i == j) ? 1.0 : 0.0;
+    A[idx] = split_df(a);
+    V[idx] = make_float2((i == j) ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   // a padding row gets a diagonal larger than every eigenvalue so it sorts last
   if (mp != m) {
-    double s = 0.0;
-    for (int idx = tid; idx < m * m; idx += nt) s += fabs(A[(idx / m) * mp + idx % m]);
+    float s = 0.f;
+    for (int idx = tid; idx < m * m; idx += nt) s += fabsf(A[(idx / m) * mp + idx % m].x);
     red[tid] = s;
     __syncthreads();
     for (int st = nt / 2; st > 0; st >>= 1) {
       if (tid < st) red[tid] += red[tid + st];
       __syncthreads();
     }
-    diag_big = 1.0 + 2.0 * red[0];
-    if (tid == 0) A[(mp - 1) * mp + (mp - 1)] = diag_big;
+    if (tid == 0) A[(mp - 1) * mp + (mp - 1)] = make_float2(1.f + 2.f * red[0], 0.f);
     __syncthreads();
   }
   const int half = mp / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // off-diagonal and total norms
-    double off = 0.0, tot = 0.0;
+    // off-diagonal and total squared norms (FP32: only the stopping test uses them)
+    float off = 0.f, tot = 0.f;
     for (int idx = tid; idx < mp * mp; idx += nt) {
-      double a = A[idx];
+      const float a = A[idx].x;
       tot += a * a;
       if (idx / mp != idx % mp) off += a * a;
     }
@@ -256,7 +374,7 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
     }
     tot = red[0];
     __syncthreads();
-    if (off <= 1e-28 * tot || off == 0.0) break;
+    if (off <= 1e-22f * tot || off == 0.f) break;
     for (int r = 0; r < mp - 1; ++r) {
       if (tid < half) {
         int k = tid;
@@ -269,17 +387,18 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
           b = ((r - k + (mp - 1)) % (mp - 1)) + 1;
         }
         int p = min(a, b), q = max(a, b);
-        double apq = A[p * mp + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300) {
-          double app = A[p * mp + p], aqq = A[q * mp + q];
-          double theta = (aqq - app) / (2.0 * apq);
-          double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
+        const float2 apq = A[p * mp + q];
+        float2 cd = make_float2(1.f, 0.f), sd = make_float2(0.f, 0.f);
+        if (apq.x != 0.f) {
+          const float2 app = A[p * mp + p], aqq = A[q * mp + q];
+          const float diff = __fadd_rn(__fsub_rn(aqq.x, app.x), __fsub_rn(aqq.y, app.y));
+          const float theta = diff / (2.f * (apq.x + apq.y));
+          const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+          const float c = rsqrtf(fmaf(t, t, 1.f));
+          df_unit_rotation(c, t * c, cd, sd);
         }
-        cs[k] = c;
-        sn[k] = s;
+        cs[k] = cd;
+        sn[k] = sd;
         pp[k] = p;
         qq[k] = q;
       }
@@ -288,44 +407,50 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
       for (int idx = tid; idx < half * mp; idx += nt) {
         int k = idx / mp, j = idx % mp;
         int p = pp[k], q = qq[k];
-        double c = cs[k], s = sn[k];
-        double ap = A[p * mp + j], aq = A[q * mp + j];
-        A[p * mp + j] = c * ap - s * aq;
-        A[q * mp + j] = s * ap + c * aq;
+        const float2 c = cs[k], s = sn[k];
+        const float2 ap = A[p * mp + j], aq = A[q * mp + j];
+        const float2 ms = make_float2(-s.x, -s.y);
+        A[p * mp + j] = df_add(df_mul(c, ap), df_mul(ms, aq));
+        A[q * mp + j] = df_add(df_mul(s, ap), df_mul(c, aq));
       }
       __syncthreads();
       // columns: A <- A J, V <- V J
       for (int idx = tid; idx < half * mp; idx += nt) {
         int k = idx / mp, i = idx % mp;
         int p = pp[k], q = qq[k];
-        double c = cs[k], s = sn[k];
-        double ap = A[i * mp + p], aq = A[i * mp + q];
-        A[i * mp + p] = c * ap - s * aq;
-        A[i * mp + q] = s * ap + c * aq;
-        double vp = V[i * mp + p], vq = V[i * mp + q];
-        V[i * mp + p] = c * vp - s * vq;
-        V[i * mp + q] = s * vp + c * vq;
+        const float2 c = cs[k], s = sn[k];
+        const float2 ms = make_float2(-s.x, -s.y);
+        const float2 ap = A[i * mp + p], aq = A[i * mp + q];
+        A[i * mp + p] = df_add(df_mul(c, ap), df_mul(ms, aq));
+        A[i * mp + q] = df_add(df_mul(s, ap), df_mul(c, aq));
+        const float2 vp = V[i * mp + p], vq = V[i * mp + q];
+        V[i * mp + p] = df_add(df_mul(c, vp), df_mul(ms, vq));
+        V[i * mp + q] = df_add(df_mul(s, vp), df_mul(c, vq));
       }
       __syncthreads();
     }
   }
-  if (tid == 0) {
-    for (int i = 0; i < m; ++i) perm[i] = i;
-    for (int i = 0; i < m; ++i) {  // selection sort of the m real eigenvalues
-      int best = i;
-      for (int j = i + 1; j < m; ++j)
-        if (A[perm[j] * mp + perm[j]] < A[perm[best] * mp + perm[best]]) best = j;
-      int t = perm[i];
-      perm[i] = perm[best];
-      perm[best] = t;
+  // ascending order of the diagonal (pairs normalised by df_add, so hi then lo orders them):
+  // rank of each entry, ties broken by index
+  for (int j = tid; j < mp; j += nt) {
+    const float2 dj = A[j * mp + j];
+    int rank = 0;
+    for (int i = 0; i < mp; ++i) {
+      const float2 di = A[i * mp + i];
+      rank += (di.x < dj.x || (di.x == dj.x && (di.y < dj.y || (di.y == dj.y && i < j)))) ? 1 : 0;
     }
+    perm[rank] = j;
   }
   __syncthreads();
   // drop the padding column: if it was not the last after sorting the pad index is m
-  for (int j = tid; j < m; j += nt) lam[j] = A[perm[j] * mp + perm[j]];
+  for (int j = tid; j < m; j += nt) {
+    const float2 d = A[perm[j] * mp + perm[j]];
+    lam[j] = (double)d.x + (double)d.y;
+  }
   for (int idx = tid; idx < m * m; idx += nt) {
     int j = idx / m, i = idx % m;
-    E[idx] = V[i * mp + perm[j]];
+    const float2 e = V[i * mp + perm[j]];
+    E[idx] = (double)e.x + (double)e.y;
   }
 }
 
@@ -813,15 +938,17 @@ struct Solver {
   void gram(const double *A, long long lda, int p, const double *B, long long ldb, int q,
             double *G, int ldg, double alpha = 1.0, double beta = 0.0) {
     const int ntp = (p + GT - 1) / GT, ntq = (q + GT - 1) / GT;
-    long long nch = std::max<long long>(1, std::min<long long>(L / 512, 304 / std::max(1, ntp * ntq) + 1));
+    // about eight 2-warp blocks per SM, chunks of at least 128 rows, partials within the scratch
+    long long nch = std::min<long long>(L / 128, (8LL * 152) / std::max(1, ntp * ntq));
+    nch = std::max<long long>(1, std::min<long long>(nch, (long long)(part_elems / std::max(1, p * q))));
     long long chunk = (L + nch - 1) / nch;
     chunk = ((chunk + GRT - 1) / GRT) * GRT;
     nch = (L + chunk - 1) / chunk;
     size_t need = (size_t)nch * p * q;
     if (need > part_elems) throw PPError(PP_ECUDA, "gram scratch too small");
-    k_gram2d<<<dim3(ntp * ntq, (unsigned)nch), 256, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, ntq, part);
+    k_gram2d<<<dim3(ntp * ntq, (unsigned)nch), 64, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, ntq, part);
     PP_LAUNCH_CHECK("k_gram2d");
-    k_gram_reduce<<<(p * q + 255) / 256, 256, 0, s>>>(part, (int)nch, p, q, G, ldg, alpha, beta);
+    k_gram_reduce<<<(p * q + 7) / 8, 256, 0, s>>>(part, (int)nch, p, q, G, ldg, alpha, beta);
     PP_LAUNCH_CHECK("k_gram_reduce");
   }
   // Y[:, 0..q) (+)= V[:, 0..m) C with C[j*ldc + i] (column j of C), columns of length L
