@@ -137,7 +137,10 @@ struct GemmOut {
   __nv_bfloat16 *Chi = nullptr, *Clo = nullptr;
   float alpha = 1.f;
   int accumulate = 0;
-  const float *add = nullptr;  // optional FP32 addend at the same offsets, times add_scale
+  // optional addend add_scale * (add_hi + add_lo)[row * add_ld + col], a BF16 pair in a
+  // row-major layout of its own
+  const __nv_bfloat16 *add_hi = nullptr, *add_lo = nullptr;
+  long long add_ld = 0;
   float add_scale = 0.f;
 };
 struct GemmArgs {
@@ -156,13 +159,19 @@ __device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float
   }
 }
 
-// 32 consecutive columns [col0, col0 + 32) of one output row: x = alpha acc (+ add_scale add[off])
+__device__ __forceinline__ float addend(const GemmOut &o, long long aoff) {
+  return o.add_scale * (__bfloat162float(o.add_hi[aoff]) + (o.add_lo ? __bfloat162float(o.add_lo[aoff]) : 0.f));
+}
+// 32 consecutive columns [col0, col0 + 32) of output row `row`: x = alpha acc (+ the addend)
 // written as FP32 (optionally accumulated) or as a BF16 pair.  Columns that run contiguously
 // (s_c0 == 1) in 16-byte-aligned groups go out 8 BF16 / 4 FP32 values per store.
 __device__ __forceinline__ bool al16(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
-__device__ void store_row32(const GemmOut &o, long long rbase, long long col0, const float *v, int N) {
+__device__ void store_row32(const GemmOut &o, long long row, long long rbase, long long col0, const float *v,
+                            int N) {
   const bool contig = o.s_c0 == 1 && (o.s_r0 % 8) == 0 && (o.s_r1 % 8) == 0 && (o.s_c1 % 8) == 0 &&
-                      (o.d_c % 8) == 0 && (!o.add || al16(o.add));
+                      (o.d_c % 8) == 0 &&
+                      (!o.add_hi || (al16(o.add_hi) && al16(o.add_lo) && (o.add_ld % 8) == 0));
+  const long long abase = row * o.add_ld;
   if (!o.C && contig && al16(o.Chi) && al16(o.Clo)) {
     for (int g = 0; g < 4; ++g) {
       const long long col = col0 + 8 * g;
@@ -170,17 +179,23 @@ __device__ void store_row32(const GemmOut &o, long long rbase, long long col0, c
       const long long off = rbase + (col / o.d_c) * o.s_c1 + (col % o.d_c);
       if (col + 8 > N) {  // ragged tail
         for (int q = 0; q < 8 && col + q < N; ++q)
-          epi_store(o, off + q, o.alpha * v[8 * g + q] + (o.add ? o.add_scale * o.add[off + q] : 0.f));
+          epi_store(o, off + q, o.alpha * v[8 * g + q] + (o.add_hi ? addend(o, abase + col + q) : 0.f));
         return;
       }
       float x[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) x[q] = o.alpha * v[8 * g + q];
-      if (o.add) {
-        const float4 a0 = *reinterpret_cast<const float4 *>(o.add + off);
-        const float4 a1 = *reinterpret_cast<const float4 *>(o.add + off + 4);
-        x[0] += o.add_scale * a0.x; x[1] += o.add_scale * a0.y; x[2] += o.add_scale * a0.z; x[3] += o.add_scale * a0.w;
-        x[4] += o.add_scale * a1.x; x[5] += o.add_scale * a1.y; x[6] += o.add_scale * a1.z; x[7] += o.add_scale * a1.w;
+      if (o.add_hi) {
+        const uint4 ah = *reinterpret_cast<const uint4 *>(o.add_hi + abase + col);
+        const uint4 al = o.add_lo ? *reinterpret_cast<const uint4 *>(o.add_lo + abase + col) : make_uint4(0, 0, 0, 0);
+        const uint32_t hw[4] = {ah.x, ah.y, ah.z, ah.w}, lw[4] = {al.x, al.y, al.z, al.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xffff0000u);
+          const float l0 = __uint_as_float(lw[q] << 16), l1 = __uint_as_float(lw[q] & 0xffff0000u);
+          x[2 * q] += o.add_scale * (h0 + l0);
+          x[2 * q + 1] += o.add_scale * (h1 + l1);
+        }
       }
       uint32_t hw[4], lw[4];
 #pragma unroll
@@ -196,7 +211,7 @@ __device__ void store_row32(const GemmOut &o, long long rbase, long long col0, c
     }
     return;
   }
-  if (o.C && contig && al16(o.C) && !o.add) {
+  if (o.C && contig && al16(o.C) && !o.add_hi) {
     for (int g = 0; g < 8; ++g) {
       const long long col = col0 + 4 * g;
       if (col >= N) return;
@@ -219,7 +234,7 @@ __device__ void store_row32(const GemmOut &o, long long rbase, long long col0, c
   for (int j = 0; j < 32; ++j) {
     if (col0 + j >= N) return;
     const long long off = rbase + cb * o.s_c1 + cr * o.s_c0;
-    epi_store(o, off, o.alpha * v[j] + (o.add ? o.add_scale * o.add[off] : 0.f));
+    epi_store(o, off, o.alpha * v[j] + (o.add_hi ? addend(o, abase + col0 + j) : 0.f));
     if (++cr == o.d_c) {
       cr = 0;
       ++cb;
@@ -318,8 +333,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
         }
         continue;
       }
-      store_row32(o, rbase, col, v, args.N);
-      if (two) store_row32(o2, rbase2, col, v, args.N);
+      store_row32(o, row, rbase, col, v, args.N);
+      if (two) store_row32(o2, row, rbase2, col, v, args.N);
     }
   }
   tc_fence_before();
@@ -716,7 +731,8 @@ struct TcPlan {
   long long ldq = 0, ldT = 0, vp = 0, Qp = 0;
   bool ready = false;  // copies of the per-dot intermediates made (after the precompute)
   KernelProfile prof;
-  int slab_i = 1, Rmax = 2;
+  int slab_i = 1, Rmax = 2;  // slab_i: occupied rows of the largest slab the buffers hold
+  int nsm = 152;             // SMs of the device (waves of the slab GEMM)
   // BF16 hi/lo operands (K-major, K padded to 64)
   DevBuf bovT_hi, bovT_lo;   // [(i,a)][ldq]       amplitude slab generator
   DevBuf bvv_hi, bvv_lo;     // [(Q,d)][vp]        W = V Bvv_Q
@@ -738,7 +754,6 @@ struct TcPlan {
   DevBuf p1_hi, p1_lo;       // P as [(r,i)][(c,Qp)]
   DevBuf p2_hi, p2_lo;       // P as [(r,a)][(k,Qp)]
   DevBuf vT_hi, vT_lo;       // V^T [(r,b)][kbo]
-  DevBuf uC;                 // U = Boo_Q V (FP32) in the layout of C_Q(V)
   DevBuf kaU_hi, kaU_lo;     // U as [(r,i)][(Q,b)]
   DevBuf efB_hi, efB_lo;     // E, F as [(r,i)][(t,j)]
   DevBuf err;
@@ -753,7 +768,7 @@ size_t tc_plan_bytes(const pp_ctx *c) {
                           &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                           &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                           &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
-                          &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                          &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo,
                           &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
   size_t n = 0;
   for (const DevBuf *b : bufs) n += b->bytes;
@@ -769,7 +784,7 @@ void tc_destroy(pp_ctx *c) {
                     &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                     &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                     &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
-                    &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo, &p->uC,
+                    &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo,
                     &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
   for (DevBuf *b : bufs) b->release();
   for (auto &v : p->prof.ev)
@@ -890,6 +905,12 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   R &= ~1LL;
   p->Rmax = (int)R;
   p->slab_i = (int)std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
+  {
+    int dev = 0, nsm = 0;
+    PP_CUDA(cudaGetDevice(&dev));
+    PP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (nsm > 0) p->nsm = nsm;
+  }
   p->err.ensure(sizeof(int) * 4);
   PP_CUDA(cudaMemsetAsync(p->err.p, 0, sizeof(int) * 4, s));
   return p;
@@ -1014,6 +1035,30 @@ void precompute_tc(pp_ctx *c) {
   precompute_finish(c);
 }
 
+// Occupied rows per slab for one sigma chunk of NC = R Q columns.  The slab GEMM P = T C^T has
+// ceil(ni v / 128) x ceil(NC / 256) tiles at one CTA per SM, so its time goes in whole waves of
+// nsm CTAs (768 tiles at 8 rows and R = 16 are 5.05 waves: the sixth runs 8 CTAs).  The height
+// that minimises the waves over all slabs -- the generator's waves weighted by their cost
+// relative to a GEMM wave, plus a small per-slab launch cost -- is taken, at most si_max.
+static int choose_slab(int o, int v, long long NC, int si_max, int nsm) {
+  const long long nt = (v + 127) / 128, ntn = (NC + 255) / 256;
+  double best = 1e300;
+  int arg = si_max;
+  for (int si = si_max; si >= 1; --si) {
+    double cost = 0.0;
+    for (int i0 = 0; i0 < o; i0 += si) {
+      const long long ni = std::min(si, o - i0);
+      const long long gt = (ni * v + 127) / 128 * ntn, tt = nt * nt * o * ni;
+      cost += (double)((gt + nsm - 1) / nsm) + 0.21 * (double)((tt + nsm - 1) / nsm) + 0.05;
+    }
+    if (cost < best - 1e-9) {
+      best = cost;
+      arg = si;
+    }
+  }
+  return arg;
+}
+
 static void ensure_zeroed(DevBuf &b, size_t bytes, cudaStream_t s) {
   if (bytes <= b.bytes) return;
   b.ensure(bytes);
@@ -1047,7 +1092,6 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     ensure_zeroed(p->efB_lo, sizeof(bf) * (size_t)Rmax * o * p->kef, s);
   }
   if (c->opt.order >= 2) {
-    p->uC.ensure(sizeof(float) * (size_t)Rmax * Q * ldT);
     ensure_zeroed(p->c_hi, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
     ensure_zeroed(p->c_lo, sizeof(bf) * (size_t)Rmax * Q * ldT, s);
     p->t_hi.ensure(sizeof(bf) * (size_t)p->slab_i * v * ldT);
@@ -1096,9 +1140,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       bf *efh = p->efB_hi.as<bf>(), *efl = p->efB_lo.as<bf>();
       const bf *A[3], *B[3];
       // U[r][Q][l][b] = sum_k Boo[Q][l][k] V[r][k][b]: rows (Q,l), columns (r,b), K = k.  Written
-      // as the BF16 pair [(r,l)][(Q,b)] (row stride kqv), the K-major operand of KA, and at
-      // second order also in FP32 in the layout of C_Q(V), [(r,Q)][(l,b)] with row stride ldT.
-      // Both layouts keep b contiguous, so each output row goes out in 16-byte stores.
+      // as the BF16 pair [(r,l)][(Q,b)] (row stride kqv), with b contiguous so that each output
+      // row leaves in 16-byte stores: the K-major operand of KA and the addend of C_Q(V)
       {
         tc::k_vT<<<tc::grid_for((long long)Rc * v * kbo), 256, 0, s>>>(V64, Rc, o, v, kbo, p->vT_hi.as<bf>(),
                                                                       p->vT_lo.as<bf>());
@@ -1113,22 +1156,11 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         ku.d_c = v;
         ku.s_c1 = (long long)o * kqv;
         ku.s_c0 = 1;
-        if (order >= 2) {
-          tc::GemmOut u;
-          u.C = p->uC.as<float>();
-          u.d_r = o;
-          u.s_r1 = ldT;
-          u.s_r0 = v;
-          u.d_c = v;
-          u.s_c1 = (long long)Q * ldT;
-          u.s_c0 = 1;
-          tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, u, err, s, &ku);
-        } else {
-          tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, ku, err, s);
-        }
+        tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, ku, err, s);
       }
       // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d), written as
-      // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction
+      // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction; U[r][Q][j][d]
+      // is element (r o + j, Q v + d) of the pair above, i.e. row * kqv + column
       if (order >= 2) {
         seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
         tc::GemmOut cc;
@@ -1140,7 +1172,9 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         cc.d_c = v;
         cc.s_c1 = ldT;
         cc.s_c0 = 1;
-        cc.add = p->uC.as<float>();
+        cc.add_hi = kuh;
+        cc.add_lo = kul;
+        cc.add_ld = kqv;
         cc.add_scale = -1.f;
         tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s);
       }
@@ -1199,7 +1233,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       bf *tlo = split ? p->t_lo.as<bf>() : nullptr;
       bf *p1h = p->p1_hi.as<bf>(), *p1l = split ? p->p1_lo.as<bf>() : nullptr;
       bf *p2h = p->p2_hi.as<bf>(), *p2l = split ? p->p2_lo.as<bf>() : nullptr;
-      const int si = p->slab_i;
+      const int si = choose_slab(o, v, NC, p->slab_i, p->nsm);
       for (int i0 = 0; i0 < o; i0 += si) {
         const int ni = std::min(si, o - i0);
         const long long rows = (long long)ni * v;
