@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ 
 // combinations of the basis are long FP64 dot products, so they run in double-FP32: each FP64
 // operand becomes an unevaluated sum hi + lo of two floats (48 significant bits), products are
 // formed with the exact FMA residual of hi * hi plus the two cross terms, and sums are kept as
-// float pairs with an error-free two-sum (relative error about 2^-46 of the sum of |terms|,
-// the level of FP64 summation over these lengths).  The operations of the two-sum carry
+// float pairs with an error-free two-sum (error within about 5e-14 of the sum of |terms| over
+// the 256-term chunk of one Gram block, set by the rounding of the float correction term;
+// the chunks are then summed in FP64).  The operations of the two-sum carry
 // explicit rounding so that no step is contracted into an FMA.
 
 // hi = the leading 24 significant bits of x (truncated), lo = x - hi rounded to float; integer
