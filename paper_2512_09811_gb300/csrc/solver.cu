@@ -321,8 +321,11 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
                                                     double *__restrict__ E, int max_sweeps) {
   extern __shared__ double sm_raw[];
   const int mp = (m + 1) & ~1;
-  float2 *A = reinterpret_cast<float2 *>(sm_raw);  // mp x mp
-  float2 *V = A + mp * mp;                          // mp x mp, eigenvectors as columns
+  // rows padded to an odd number of 8-byte words: a column of A or V read across a warp
+  // then falls in distinct shared-memory banks
+  const int ld = mp + 1;
+  float2 *A = reinterpret_cast<float2 *>(sm_raw);  // mp x ld
+  float2 *V = A + mp * ld;                          // mp x ld, eigenvectors as columns
   __shared__ float2 cs[MAXM / 2], sn[MAXM / 2];
   __shared__ int pp[MAXM / 2], qq[MAXM / 2];
   __shared__ float red[512];
@@ -333,21 +336,21 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
     double a;
     if (i < m && j < m) a = 0.5 * (Gin[i * m + j] + Gin[j * m + i]);
     else a = 0.0;
-    A[idx] = split_df(a);
-    V[idx] = make_float2((i == j) ? 1.f : 0.f, 0.f);
+    A[i * ld + j] = split_df(a);
+    V[i * ld + j] = make_float2((i == j) ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   // a padding row gets a diagonal larger than every eigenvalue so it sorts last
   if (mp != m) {
     float s = 0.f;
-    for (int idx = tid; idx < m * m; idx += nt) s += fabsf(A[(idx / m) * mp + idx % m].x);
+    for (int idx = tid; idx < m * m; idx += nt) s += fabsf(A[(idx / m) * ld + idx % m].x);
     red[tid] = s;
     __syncthreads();
     for (int st = nt / 2; st > 0; st >>= 1) {
       if (tid < st) red[tid] += red[tid + st];
       __syncthreads();
     }
-    if (tid == 0) A[(mp - 1) * mp + (mp - 1)] = make_float2(1.f + 2.f * red[0], 0.f);
+    if (tid == 0) A[(mp - 1) * ld + (mp - 1)] = make_float2(1.f + 2.f * red[0], 0.f);
     __syncthreads();
   }
   const int half = mp / 2;
@@ -355,7 +358,7 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
     // off-diagonal and total squared norms (FP32: only the stopping test uses them)
     float off = 0.f, tot = 0.f;
     for (int idx = tid; idx < mp * mp; idx += nt) {
-      const float a = A[idx].x;
+      const float a = A[(idx / mp) * ld + idx % mp].x;
       tot += a * a;
       if (idx / mp != idx % mp) off += a * a;
     }
@@ -388,10 +391,10 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
           b = ((r - k + (mp - 1)) % (mp - 1)) + 1;
         }
         int p = min(a, b), q = max(a, b);
-        const float2 apq = A[p * mp + q];
+        const float2 apq = A[p * ld + q];
         float2 cd = make_float2(1.f, 0.f), sd = make_float2(0.f, 0.f);
         if (apq.x != 0.f) {
-          const float2 app = A[p * mp + p], aqq = A[q * mp + q];
+          const float2 app = A[p * ld + p], aqq = A[q * ld + q];
           const float diff = __fadd_rn(__fsub_rn(aqq.x, app.x), __fsub_rn(aqq.y, app.y));
           const float theta = diff / (2.f * (apq.x + apq.y));
           const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
@@ -409,10 +412,10 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
         int k = idx / mp, j = idx % mp;
         int p = pp[k], q = qq[k];
         const float2 c = cs[k], s = sn[k];
-        const float2 ap = A[p * mp + j], aq = A[q * mp + j];
+        const float2 ap = A[p * ld + j], aq = A[q * ld + j];
         const float2 ms = make_float2(-s.x, -s.y);
-        A[p * mp + j] = df_add(df_mul(c, ap), df_mul(ms, aq));
-        A[q * mp + j] = df_add(df_mul(s, ap), df_mul(c, aq));
+        A[p * ld + j] = df_add(df_mul(c, ap), df_mul(ms, aq));
+        A[q * ld + j] = df_add(df_mul(s, ap), df_mul(c, aq));
       }
       __syncthreads();
       // columns: A <- A J, V <- V J
@@ -421,12 +424,12 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
         int p = pp[k], q = qq[k];
         const float2 c = cs[k], s = sn[k];
         const float2 ms = make_float2(-s.x, -s.y);
-        const float2 ap = A[i * mp + p], aq = A[i * mp + q];
-        A[i * mp + p] = df_add(df_mul(c, ap), df_mul(ms, aq));
-        A[i * mp + q] = df_add(df_mul(s, ap), df_mul(c, aq));
-        const float2 vp = V[i * mp + p], vq = V[i * mp + q];
-        V[i * mp + p] = df_add(df_mul(c, vp), df_mul(ms, vq));
-        V[i * mp + q] = df_add(df_mul(s, vp), df_mul(c, vq));
+        const float2 ap = A[i * ld + p], aq = A[i * ld + q];
+        A[i * ld + p] = df_add(df_mul(c, ap), df_mul(ms, aq));
+        A[i * ld + q] = df_add(df_mul(s, ap), df_mul(c, aq));
+        const float2 vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = df_add(df_mul(c, vp), df_mul(ms, vq));
+        V[i * ld + q] = df_add(df_mul(s, vp), df_mul(c, vq));
       }
       __syncthreads();
     }
@@ -434,10 +437,10 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
   // ascending order of the diagonal (pairs normalised by df_add, so hi then lo orders them):
   // rank of each entry, ties broken by index
   for (int j = tid; j < mp; j += nt) {
-    const float2 dj = A[j * mp + j];
+    const float2 dj = A[j * ld + j];
     int rank = 0;
     for (int i = 0; i < mp; ++i) {
-      const float2 di = A[i * mp + i];
+      const float2 di = A[i * ld + i];
       rank += (di.x < dj.x || (di.x == dj.x && (di.y < dj.y || (di.y == dj.y && i < j)))) ? 1 : 0;
     }
     perm[rank] = j;
@@ -445,12 +448,12 @@ __global__ void __launch_bounds__(512) k_jacobi_eig(const double *__restrict__ G
   __syncthreads();
   // drop the padding column: if it was not the last after sorting the pad index is m
   for (int j = tid; j < m; j += nt) {
-    const float2 d = A[perm[j] * mp + perm[j]];
+    const float2 d = A[perm[j] * ld + perm[j]];
     lam[j] = (double)d.x + (double)d.y;
   }
   for (int idx = tid; idx < m * m; idx += nt) {
     int j = idx / m, i = idx % m;
-    const float2 e = V[i * mp + perm[j]];
+    const float2 e = V[i * ld + perm[j]];
     E[idx] = (double)e.x + (double)e.y;
   }
 }
@@ -1108,7 +1111,7 @@ struct WindowBatch {
       wi.dkept = wi.dstat + 4;
     }
     const int ld = MAXM + 1;
-    const int smem_jac = 2 * MAXM * MAXM * (int)sizeof(double);
+    const int smem_jac = 2 * MAXM * (MAXM + 1) * (int)sizeof(double);
     const int smem_chol = (MAXM * ld + 2 * MAXM) * (int)sizeof(double);
     const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
     PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
@@ -1315,7 +1318,7 @@ struct WindowBatch {
     k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(wi.Yw, wi.Lm, wi.dinv, m, 1, wi.Cw, wi.dstat);
     PP_LAUNCH_CHECK("k_rr_trsm");
     int mp = (m + 1) & ~1;
-    k_jacobi_eig<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
+    k_jacobi_eig<<<1, 512, 2 * mp * (mp + 1) * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
     PP_LAUNCH_CHECK("k_jacobi_eig");
     const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
     k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);

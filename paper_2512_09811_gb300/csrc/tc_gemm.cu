@@ -173,6 +173,18 @@ __device__ void store_row32(const GemmOut &o, long long row, long long rbase, lo
                       (!o.add_hi || (al16(o.add_hi) && al16(o.add_lo) && (o.add_ld % 8) == 0));
   const long long abase = row * o.add_ld;
   if (!o.C && contig && al16(o.Chi) && al16(o.Clo)) {
+    // a full chunk's addend is loaded before any of its stores, so that its eight 16-byte
+    // loads are in flight together
+    uint4 pah[4], pal[4];
+    const bool pre = o.add_hi && col0 + 32 <= N;
+    if (pre) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        pah[g] = *reinterpret_cast<const uint4 *>(o.add_hi + abase + col0 + 8 * g);
+        pal[g] = o.add_lo ? *reinterpret_cast<const uint4 *>(o.add_lo + abase + col0 + 8 * g) : make_uint4(0, 0, 0, 0);
+      }
+    }
+#pragma unroll
     for (int g = 0; g < 4; ++g) {
       const long long col = col0 + 8 * g;
       if (col >= N) return;
@@ -186,8 +198,9 @@ __device__ void store_row32(const GemmOut &o, long long row, long long rbase, lo
 #pragma unroll
       for (int q = 0; q < 8; ++q) x[q] = o.alpha * v[8 * g + q];
       if (o.add_hi) {
-        const uint4 ah = *reinterpret_cast<const uint4 *>(o.add_hi + abase + col);
-        const uint4 al = o.add_lo ? *reinterpret_cast<const uint4 *>(o.add_lo + abase + col) : make_uint4(0, 0, 0, 0);
+        const uint4 ah = pre ? pah[g] : *reinterpret_cast<const uint4 *>(o.add_hi + abase + col);
+        const uint4 al = pre ? pal[g]
+                             : (o.add_lo ? *reinterpret_cast<const uint4 *>(o.add_lo + abase + col) : make_uint4(0, 0, 0, 0));
         const uint32_t hw[4] = {ah.x, ah.y, ah.z, ah.w}, lw[4] = {al.x, al.y, al.z, al.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
