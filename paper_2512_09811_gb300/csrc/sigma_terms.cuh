@@ -52,6 +52,13 @@ __global__ void k_gap_scale(T *__restrict__ out, const T *__restrict__ gap, cons
        p += (long long)gridDim.x * blockDim.x)
     out[p] = gap[p % ov] * V[p];
 }
+// acc += x
+template <class T>
+__global__ void k_add(T *__restrict__ acc, const T *__restrict__ x, long long total) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x)
+    acc[p] += x[p];
+}
 // U[r][Q][j][d] <- W[r][j][Q][d] - U[r][Q][j][d]
 template <class T>
 __global__ void k_cmat(T *__restrict__ U, const T *__restrict__ W, int o, int v, int Q, long long total) {
@@ -146,14 +153,14 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
       g.ksplit = 32;
     }
     gemm<T>(g, s);
-    GemmS<T> j;  // J into both accumulators
-    j.M = R; j.N = (int)ov; j.K = Q;
+    GemmS<T> j;  // J, the same term in both accumulators: formed once in Bacc (still zero),
+    j.M = R; j.N = (int)ov; j.K = Q;  // then added to Aacc
     j.A = cq; j.a_m = 1; j.a_k = R;
     j.B = res.Bov; j.b_k = ov; j.b_n = 1;
-    j.C = Aacc; j.c_m = ov; j.c_n = 1; j.beta = T(1);
+    j.C = Bacc; j.c_m = ov; j.c_n = 1; j.beta = T(1);
     gemm<T>(j, s);
-    j.C = Bacc;
-    gemm<T>(j, s);
+    k_add<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, Bacc, tot);
+    PP_LAUNCH_CHECK("k_add");
     if (hk.first_order && hk.first_order(R, Aacc, Bacc)) {
       if (order >= 2) hk.amplitude(R, nullptr, Bacc);
     } else {
