@@ -241,6 +241,209 @@ __global__ void __launch_bounds__(256) k_combine_ts(const double *__restrict__ V
   }
 }
 
+// ---- FP64 forms of the Gram, combination and Jacobi kernels ---------------------------------
+// Contexts of the FP64 form converge to tight residuals (1e-8 and below), where the folded
+// extraction resolves neighbouring roots only if its Grams carry FP64-level accuracy: their
+// smallest eigenvalues sit at the squared residual.  These contexts keep the Krylov-space
+// arithmetic in FP64 (at the FP64 issue rate); the mixed form (residual 1e-6) uses the
+// double-FP32 kernels above.
+__global__ void __launch_bounds__(256) k_gram2d_f64(const double *__restrict__ A, long long lda, int p,
+                                                const double *__restrict__ B, long long ldb, int q,
+                                                long long L, long long chunk, int ntq,
+                                                double *__restrict__ part) {
+  __shared__ double As[GT][GRT + 1];
+  __shared__ double Bs[GT][GRT + 1];
+  const int ti = blockIdx.x / ntq, tj = blockIdx.x % ntq;
+  const int i0 = ti * GT, j0 = tj * GT;
+  const long long l0 = blockIdx.y * chunk, l1 = min(L, l0 + chunk);
+  const int tid = threadIdx.x;
+  const int oi = tid >> 3, oj = (tid & 7) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long r0 = l0; r0 < l1; r0 += GRT) {
+    for (int idx = tid; idx < GT * GRT; idx += 256) {
+      int i = idx / GRT, rr = idx % GRT;
+      long long l = r0 + rr;
+      As[i][rr] = (i0 + i < p && l < l1) ? A[(long long)(i0 + i) * lda + l] : 0.0;
+      Bs[i][rr] = (j0 + i < q && l < l1) ? B[(long long)(j0 + i) * ldb + l] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GRT; ++rr) {
+      const double a = As[oi][rr];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] = fma(a, Bs[oj + t][rr], acc[t]);
+    }
+    __syncthreads();
+  }
+  const long long base = (long long)blockIdx.y * p * q;
+  for (int t = 0; t < 4; ++t) {
+    const int i = i0 + oi, j = j0 + oj + t;
+    if (i < p && j < q) part[base + (long long)i * q + j] = acc[t];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_combine_ts_f64(const double *__restrict__ V, long long ldv, int m,
+                                                    const double *__restrict__ C, int ldc, int q,
+                                                    double *__restrict__ Y, long long ldy, long long L,
+                                                    double alpha, double beta) {
+  __shared__ double Cs[CTS][MAXM];
+  const int j0 = blockIdx.y * CTS;
+  const int nj = min(CTS, q - j0);
+  for (int idx = threadIdx.x; idx < nj * m; idx += blockDim.x) {
+    int j = idx / m, k = idx % m;
+    Cs[j][k] = C[(long long)(j0 + j) * ldc + k];
+  }
+  __syncthreads();
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double acc[CTS];
+#pragma unroll
+  for (int j = 0; j < CTS; ++j) acc[j] = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double vk = V[(long long)k * ldv + l];
+#pragma unroll
+    for (int j = 0; j < CTS; ++j) acc[j] = fma(vk, Cs[j][k], acc[j]);
+  }
+  for (int j = 0; j < nj; ++j) {
+    double *y = Y + (long long)(j0 + j) * ldy + l;
+    *y = alpha * acc[j] + (beta != 0.0 ? beta * (*y) : 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(512) k_jacobi_eig_f64(const double *__restrict__ Gin, int m,
+                                                    double *__restrict__ lam,
+                                                    double *__restrict__ E, int max_sweeps) {
+  extern __shared__ double sm[];
+  const int mp = (m + 1) & ~1;
+  double *A = sm;            // mp x mp
+  double *V = sm + mp * mp;  // mp x mp, eigenvectors as columns
+  __shared__ double cs[MAXM / 2], sn[MAXM / 2];
+  __shared__ int pp[MAXM / 2], qq[MAXM / 2];
+  __shared__ double red[512];
+  __shared__ int perm[MAXM];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double diag_big = 0.0;
+  for (int idx = tid; idx < mp * mp; idx += nt) {
+    int i = idx / mp, j = idx % mp;
+    double a;
+    if (i < m && j < m) a = 0.5 * (Gin[i * m + j] + Gin[j * m + i]);
+    else a = 0.0;
+    A[idx] = a;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // a padding row gets a diagonal larger than every eigenvalue so it sorts last
+  if (mp != m) {
+    double s = 0.0;
+    for (int idx = tid; idx < m * m; idx += nt) s += fabs(A[(idx / m) * mp + idx % m]);
+    red[tid] = s;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    diag_big = 1.0 + 2.0 * red[0];
+    if (tid == 0) A[(mp - 1) * mp + (mp - 1)] = diag_big;
+    __syncthreads();
+  }
+  const int half = mp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // off-diagonal and total norms
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < mp * mp; idx += nt) {
+      double a = A[idx];
+      tot += a * a;
+      if (idx / mp != idx % mp) off += a * a;
+    }
+    red[tid] = off;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    off = red[0];
+    __syncthreads();
+    red[tid] = tot;
+    __syncthreads();
+    for (int st = nt / 2; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
+      __syncthreads();
+    }
+    tot = red[0];
+    __syncthreads();
+    if (off <= 1e-28 * tot || off == 0.0) break;
+    for (int r = 0; r < mp - 1; ++r) {
+      if (tid < half) {
+        int k = tid;
+        int a, b;
+        if (k == 0) {
+          a = 0;
+          b = (r % (mp - 1)) + 1;
+        } else {
+          a = ((r + k) % (mp - 1)) + 1;
+          b = ((r - k + (mp - 1)) % (mp - 1)) + 1;
+        }
+        int p = min(a, b), q = max(a, b);
+        double apq = A[p * mp + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300) {
+          double app = A[p * mp + p], aqq = A[q * mp + q];
+          double theta = (aqq - app) / (2.0 * apq);
+          double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+        }
+        cs[k] = c;
+        sn[k] = s;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = tid; idx < half * mp; idx += nt) {
+        int k = idx / mp, j = idx % mp;
+        int p = pp[k], q = qq[k];
+        double c = cs[k], s = sn[k];
+        double ap = A[p * mp + j], aq = A[q * mp + j];
+        A[p * mp + j] = c * ap - s * aq;
+        A[q * mp + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = tid; idx < half * mp; idx += nt) {
+        int k = idx / mp, i = idx % mp;
+        int p = pp[k], q = qq[k];
+        double c = cs[k], s = sn[k];
+        double ap = A[i * mp + p], aq = A[i * mp + q];
+        A[i * mp + p] = c * ap - s * aq;
+        A[i * mp + q] = s * ap + c * aq;
+        double vp = V[i * mp + p], vq = V[i * mp + q];
+        V[i * mp + p] = c * vp - s * vq;
+        V[i * mp + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    for (int i = 0; i < m; ++i) {  // selection sort of the m real eigenvalues
+      int best = i;
+      for (int j = i + 1; j < m; ++j)
+        if (A[perm[j] * mp + perm[j]] < A[perm[best] * mp + perm[best]]) best = j;
+      int t = perm[i];
+      perm[i] = perm[best];
+      perm[best] = t;
+    }
+  }
+  __syncthreads();
+  // drop the padding column: if it was not the last after sorting the pad index is m
+  for (int j = tid; j < m; j += nt) lam[j] = A[perm[j] * mp + perm[j]];
+  for (int idx = tid; idx < m * m; idx += nt) {
+    int j = idx / m, i = idx % m;
+    E[idx] = V[i * mp + perm[j]];
+  }
+}
+
 // ---- Cholesky QR of a block: G = N^T N (n x n); T (row j = coefficients of new vector j) with
 // N_new_j = sum_k N_k T[j][k]; columns whose pivot falls below tol * G_jj are dropped (T row 0,
 // kept[j] = 0).  One thread (n <= 64).
@@ -938,10 +1141,23 @@ struct Solver {
   long long L;  // 2 ov
   double *part = nullptr;
   size_t part_elems = 0;
+  bool f64 = false;  // FP64 Krylov-space arithmetic (contexts of the FP64 form)
 
   void gram(const double *A, long long lda, int p, const double *B, long long ldb, int q,
             double *G, int ldg, double alpha = 1.0, double beta = 0.0) {
     const int ntp = (p + GT - 1) / GT, ntq = (q + GT - 1) / GT;
+    if (f64) {
+      long long nch = std::max<long long>(1, std::min<long long>(L / 512, 304 / std::max(1, ntp * ntq) + 1));
+      long long chunk = (L + nch - 1) / nch;
+      chunk = ((chunk + GRT - 1) / GRT) * GRT;
+      nch = (L + chunk - 1) / chunk;
+      if ((size_t)nch * p * q > part_elems) throw PPError(PP_ECUDA, "gram scratch too small");
+      k_gram2d_f64<<<dim3(ntp * ntq, (unsigned)nch), 256, 0, s>>>(A, lda, p, B, ldb, q, L, chunk, ntq, part);
+      PP_LAUNCH_CHECK("k_gram2d_f64");
+      k_gram_reduce<<<(p * q + 7) / 8, 256, 0, s>>>(part, (int)nch, p, q, G, ldg, alpha, beta);
+      PP_LAUNCH_CHECK("k_gram_reduce");
+      return;
+    }
     // about eight 2-warp blocks per SM, chunks of at least 128 rows, partials within the scratch
     long long nch = std::min<long long>(L / 128, (8LL * 152) / std::max(1, ntp * ntq));
     nch = std::max<long long>(1, std::min<long long>(nch, (long long)(part_elems / std::max(1, p * q))));
@@ -960,7 +1176,10 @@ struct Solver {
                double beta) {
     if (m <= MAXM) {
       dim3 grid((unsigned)((L + 255) / 256), (unsigned)((q + CTS - 1) / CTS));
-      k_combine_ts<<<grid, 256, 0, s>>>(V, L, m, C, ldc, q, Y, L, L, alpha, beta);
+      if (f64)
+        k_combine_ts_f64<<<grid, 256, 0, s>>>(V, L, m, C, ldc, q, Y, L, L, alpha, beta);
+      else
+        k_combine_ts<<<grid, 256, 0, s>>>(V, L, m, C, ldc, q, Y, L, L, alpha, beta);
       PP_LAUNCH_CHECK("k_combine_ts");
       return;
     }
@@ -1062,6 +1281,7 @@ struct WindowBatch {
     m_max = std::min<int>(std::min(c->opt.m_max, MAXM), (int)L);
     bcap = std::max(1, std::min(32, m_max / 3));
     prec0 = c->opt.prec;
+    sv.f64 = (prec0 == PP_FP64);
     refine = (prec0 == PP_BF16) && c->opt.refine;
     std::vector<double> hA(ov), hS(ov);
     PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
@@ -1115,6 +1335,8 @@ struct WindowBatch {
     const int smem_chol = (MAXM * ld + 2 * MAXM) * (int)sizeof(double);
     const int smem_ref = (MAXM * ld + 2 * 32 * MAXM + 3 * MAXM) * (int)sizeof(double);
     PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_jac));
+    PP_CUDA(cudaFuncSetAttribute(k_jacobi_eig_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * MAXM * MAXM * (int)sizeof(double)));
     PP_CUDA(cudaFuncSetAttribute(k_chol_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_chol));
     PP_CUDA(cudaFuncSetAttribute(k_refined, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ref));
     const char *log_env = std::getenv("PP_LOG");
@@ -1318,7 +1540,10 @@ struct WindowBatch {
     k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(wi.Yw, wi.Lm, wi.dinv, m, 1, wi.Cw, wi.dstat);
     PP_LAUNCH_CHECK("k_rr_trsm");
     int mp = (m + 1) & ~1;
-    k_jacobi_eig<<<1, 512, 2 * mp * (mp + 1) * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
+    if (sv.f64)
+      k_jacobi_eig_f64<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
+    else
+      k_jacobi_eig<<<1, 512, 2 * mp * (mp + 1) * sizeof(double), s>>>(wi.Cw, m, wi.mu, wi.W, 16);
     PP_LAUNCH_CHECK("k_jacobi_eig");
     const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
     k_rr_select<<<1, 128, 0, s>>>(wi.Lm, wi.mu, wi.W, m, wi.shift, nsel, wi.Ew, wi.thsel, wi.Esel);
