@@ -38,46 +38,6 @@ namespace {
 
 constexpr int MAXM = 112;  // largest subspace the shared-memory eigensolver takes
 
-// ---- tall-skinny Gram: partial[blk][i][j] = sum_{l in chunk} A_i[l] B_j[l] -------------
-constexpr int GR_ROWS = 16;
-__global__ void __launch_bounds__(256) k_gram(const double *__restrict__ A, long long lda, int p,
-                                              const double *__restrict__ B, long long ldb, int q,
-                                              long long L, long long chunk, double *__restrict__ part) {
-  __shared__ double As[MAXM][GR_ROWS + 1];
-  __shared__ double Bs[MAXM][GR_ROWS + 1];
-  const long long l0 = blockIdx.x * chunk;
-  const long long l1 = min(L, l0 + chunk);
-  const int npair = p * q;
-  double acc[(MAXM * MAXM + 255) / 256];
-  const int mine = (npair - (int)threadIdx.x + 255) / 256;
-  for (int e = 0; e < (MAXM * MAXM + 255) / 256; ++e) acc[e] = 0.0;
-  for (long long r0 = l0; r0 < l1; r0 += GR_ROWS) {
-    for (int idx = threadIdx.x; idx < p * GR_ROWS; idx += 256) {
-      int i = idx / GR_ROWS, rr = idx % GR_ROWS;
-      long long l = r0 + rr;
-      As[i][rr] = (l < l1) ? A[i * lda + l] : 0.0;
-    }
-    for (int idx = threadIdx.x; idx < q * GR_ROWS; idx += 256) {
-      int j = idx / GR_ROWS, rr = idx % GR_ROWS;
-      long long l = r0 + rr;
-      Bs[j][rr] = (l < l1) ? B[j * ldb + l] : 0.0;
-    }
-    __syncthreads();
-    for (int e = 0; e < mine; ++e) {
-      int pr = threadIdx.x + e * 256;
-      int i = pr / q, j = pr % q;
-      double s = acc[e];
-#pragma unroll
-      for (int rr = 0; rr < GR_ROWS; ++rr) s = fma(As[i][rr], Bs[j][rr], s);
-      acc[e] = s;
-    }
-    __syncthreads();
-  }
-  for (int e = 0; e < mine; ++e) {
-    int pr = threadIdx.x + e * 256;
-    part[(long long)blockIdx.x * npair + pr] = acc[e];
-  }
-}
 // one warp per output: the partials are summed lane-strided, then across the warp
 __global__ void __launch_bounds__(256) k_gram_reduce(const double *__restrict__ part, int nblk, int p, int q,
                                                      double *__restrict__ G, int ldg, double alpha, double beta) {
@@ -722,18 +682,6 @@ __global__ void k_resid_dir(const double *__restrict__ X, const double *__restri
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) rnorm[blockIdx.x] = acc;
-}
-
-// y_j <- y_j * s for three arrays, with s = 1/sqrt(nrm[0])
-__global__ void k_scale3(double *__restrict__ a, double *__restrict__ b, double *__restrict__ c,
-                         long long L, const double *__restrict__ nrm2) {
-  double s = 1.0 / sqrt(nrm2[0]);
-  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < L;
-       l += (long long)gridDim.x * blockDim.x) {
-    a[l] *= s;
-    b[l] *= s;
-    c[l] *= s;
-  }
 }
 
 // oscillator strengths: z = x / sqrt(x^T Sigma x); out[j] = (2/3) theta sum_c (mu_c . (X + Y))^2
