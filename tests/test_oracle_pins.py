@@ -183,3 +183,62 @@ def test_window_selection_rules():
     assert list(po.select_window(om, 1.0, 0.25, 2, 0)) == [2, 3]
     assert list(po.select_window(om, 1.0, 0.25, 5, 0)) == [2, 3, 4]
     assert list(po.select_window(om, 1.0, 0.0, 3, 1)) == [1, 2, 3]
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_oscillator_strength_sum_rule(tiny, order):
+    """RPA sum rule (Eq. pp_adc with F = mu): over all roots,
+    sum_n omega_n (mu_c . (X_n + Y_n))^2 = mu_c^T S^-1 (A - B) S^-1 mu_c, so
+    sum_n f_n = (2/3) sum_c mu_c^T S^-1 (A - B) S^-1 mu_c.
+
+    Derived from the Cholesky-reduced form: with u_n = L^T (X_n + Y_n) and
+    v_n = L^T (X_n - Y_n), (At - Bt) v_n = omega_n u_n, u_m^T v_n = delta_mn, so
+    sum_n omega_n u_n u_n^T = At - Bt.  The X - Y combination would give the
+    (A + B) form instead, and a wrong power of omega or a missing 2/3 changes
+    the sum; B is non-zero at orders 1 and 2, so each slip fails here.
+    """
+    o = tiny.nocc
+    S, A, Bm = po.dense_blocks(tiny.eps, tiny.B, o, order=order)
+    res = po.solve_dense(S, A, Bm, tiny.mu)
+    Si = np.linalg.inv(S)
+    mu = tiny.mu.reshape(3, -1)
+    want = (2.0 / 3.0) * sum(m @ Si @ (A - Bm) @ Si @ m for m in mu)
+    np.testing.assert_allclose(res["f"].sum(), want, rtol=1e-10)
+    # the X - Y slip is detectable at this size (its sum is the A + B form)
+    slip = (2.0 / 3.0) * sum(m @ Si @ (A + Bm) @ Si @ m for m in mu)
+    assert abs(slip - want) > 1e-3 * abs(want)
+    # per root: f_n >= 0, and the zero-dipole vector gives f = 0
+    assert np.all(res["f"] >= 0)
+    np.testing.assert_array_equal(po.oscillator_strengths(res["omega"], res["X"], res["Y"], 0 * tiny.mu), 0.0)
+
+
+def test_variance_hand_values():
+    """Sec. 4.2 variance on vectors that are not eigenvectors, against hand-computed values.
+
+    (1) M = diag(1, 3), Sigma = 1, z = (1, 1), theta = 2: r = (-1, 1), |r|^2 / |z|^2 = 1,
+        which is rho_{A^2} - rho_A^2 = 5 - 4 of the paper's definition.
+    (2) M = [[2, 1], [1, 2]], Sigma = diag(1, -1), z = (1, 0), theta = 1:
+        M z = (2, 1), Sigma z = (1, 0), r = (1, 1), so the variance is 2.
+    (3) z scaled by 3: the variance is normalised by |z|^2, so it is unchanged.
+    """
+    M1 = np.diag([1.0, 3.0])
+    assert po.variance(M1, np.eye(2), np.array([1.0, 1.0]), 2.0) == pytest.approx(1.0, abs=1e-15)
+    M2 = np.array([[2.0, 1.0], [1.0, 2.0]])
+    Sg = np.diag([1.0, -1.0])
+    assert po.variance(M2, Sg, np.array([1.0, 0.0]), 1.0) == pytest.approx(2.0, abs=1e-15)
+    assert po.variance(M2, Sg, np.array([3.0, 0.0]), 1.0) == pytest.approx(2.0, abs=1e-14)
+
+
+def test_variance_is_paper_definition_for_unit_metric():
+    """With Sigma = 1 and theta the Rayleigh quotient, the variance equals
+    rho_{A^2}(x) - rho_A(x)^2 (Sec. 4.2), computed here from A^2 directly."""
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(7, 7))
+    A = A + A.T
+    for _ in range(5):
+        x = rng.normal(size=7)
+        xn = x / np.linalg.norm(x)
+        rho = xn @ A @ xn
+        rho2 = xn @ (A @ A) @ xn
+        assert po.variance(A, np.eye(7), x, rho) == pytest.approx(rho2 - rho * rho, rel=1e-12)
+        assert rho2 - rho * rho > 1e-3  # not an eigenvector
