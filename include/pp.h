@@ -134,17 +134,22 @@ pp_status pp_sigma(pp_ctx *ctx, int nvec, const double *Z, double *sigma, double
  *   nvec * nocc * nvir must not exceed PP_METRIC_NOALLOC_MAX_ELEMS: the two
  *           intermediate products live in one fixed 16 MiB array per device compiled
  *           into the library.  Larger batches return PP_EINVAL with the sizes in
- *           pp_last_error; split them, or use pp_sigma.
+ *           pp_last_error; split them, or use pp_sigma.  nvec must also not exceed
+ *           PP_METRIC_NOALLOC_MAX_NVEC (the 2 nvec half-vectors are one grid dimension).
+ *   The current device must be the context's device (the one current at pp_create),
+ *           else PP_EINVAL; Z and out must be that device's memory.
  *   The array is shared by all contexts and calls on a device: calls that overlap in
  *   time on one device (several host threads, or streams running concurrently) race
  *   on it and may return wrong results, so serialise them.  Nothing in it needs to
  *   start at zero.
  *   Set-up: the first call on each device (nvec = 0 does only the set-up) looks the
- *   array's address up with that device current; it can load the library's device
- *   code, so it must precede any stream capture on that device.
+ *   array's address up with that device current and has the runtime load the kernels
+ *   the call launches; it can load the library's device code, so it must precede any
+ *   stream capture on that device.  Later calls load nothing.
  * Runs on the context's stream and returns after that stream has finished the work.
  */
 #define PP_METRIC_NOALLOC_MAX_ELEMS (1LL << 19)
+#define PP_METRIC_NOALLOC_MAX_NVEC 32767
 pp_status pp_metric_noalloc(pp_ctx *ctx, int nvec, const double *Z, double *out);
 
 /*
@@ -176,6 +181,24 @@ pp_status pp_solve_window(pp_ctx *ctx, double omega0, double delta, int k, doubl
 pp_status pp_solve_windows(pp_ctx *ctx, int nwin, const double *omega0, const double *delta,
                            const int *k, double *omega, double *osc, double *resid, int *nfound);
 
+/*
+ * The same batched solve driven one block iteration at a time (for callers that interleave
+ * other work, and for timing single iterations).  pp_windows_begin places the windows in the
+ * context's window slots (arguments as pp_solve_windows; an earlier batch that was not
+ * collected is abandoned).  Each pp_windows_step runs one iteration of every unfinished
+ * window -- Rayleigh-Ritz and the folded extraction, residuals, Jacobi directions, block
+ * CGS2, and one sigma batch per precision phase for the new vectors of all windows (Sec.
+ * 2.5) -- and returns after the context's stream is idle; *unfinished receives the windows
+ * still running, *sigma_vectors the supervectors multiplied in this step and *sigma_calls
+ * the sigma batches applied (any of them may be NULL).  A step with no unfinished window
+ * does nothing.  pp_windows_end, once no window is unfinished, writes the results as
+ * pp_solve_windows does and releases the slots (PP_EINVAL while windows are running;
+ * PP_ENOTCONV if a window reached max_iter).
+ */
+pp_status pp_windows_begin(pp_ctx *ctx, int nwin, const double *omega0, const double *delta, const int *k);
+pp_status pp_windows_step(pp_ctx *ctx, int *unfinished, long long *sigma_vectors, int *sigma_calls);
+pp_status pp_windows_end(pp_ctx *ctx, double *omega, double *osc, double *resid, int *nfound);
+
 /* Statistics of the last solve: outer iterations, sigma supervectors applied,
    milliseconds spent in sigma and in the whole solve. */
 pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vectors,
@@ -188,8 +211,11 @@ pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vec
  * stream; pp_profile(ctx, 0) stops recording.  pp_profile_read returns, for
  * kernel id 0 (the amplitude contraction GEMM, Eq. (b(2)) ladder and ring
  * parts) or id 1 (the amplitude slab generator, MP2 t of Sec. 2.2), the number
- * of launches, their summed device milliseconds and their algorithmic FLOPs
- * (2 M N K per tensor-core product; K excludes the zero padding).
+ * of launches, their summed device milliseconds and their algorithmic FLOPs: each
+ * contraction counted once, 2 M N K with K excluding the zero padding; the three BF16
+ * products of the split (refinement) form count as one, and the generator counts one
+ * Q-long product per amplitude (the exchange integral (id|jc) of t_ij^cd is the direct
+ * integral of t_ij^dc).
  */
 pp_status pp_profile(pp_ctx *ctx, int enable);
 pp_status pp_profile_read(pp_ctx *ctx, int id, long long *launches, double *ms, double *flops);
@@ -241,7 +267,9 @@ typedef struct {
  */
 pp_status pp_server_create(size_t hbm_budget, const pp_options *opt, int slots_per_dot, int nworkers,
                            pp_server **out);
-/* Register a dot (arguments as pp_create; inputs are copied).  *dot_id numbers dots from 0. */
+/* Register a dot (arguments as pp_create; inputs are copied).  *dot_id numbers dots from 0.
+   Returns PP_ENOMEM (message in pp_server_last_error) if the dot's estimated device footprint
+   alone exceeds hbm_budget: such a dot could never be admitted. */
 pp_status pp_server_add_dot(pp_server *srv, int nocc, int nvir, int naux, const double *eps, const void *B,
                             int B_dtype, const double *mu, int *dot_id);
 /* Queue a window request (arguments as pp_solve_window, select rule from the options). */

@@ -28,7 +28,7 @@ STATUS_NAMES = {
 # every symbol declared in include/pp.h
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
-    "pp_solve_windows", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
+    "pp_solve_windows", "pp_windows_begin", "pp_windows_step", "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
     "pp_last_error", "pp_server_create", "pp_server_add_dot", "pp_server_submit", "pp_server_wait",
     "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
 )
@@ -91,6 +91,12 @@ def load(path: str | None = None):
         lib.pp_solve_windows.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int), _dp, _dp, _dp,
                                          C.POINTER(C.c_int)]
         lib.pp_solve_windows.restype = C.c_int
+        lib.pp_windows_begin.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
+        lib.pp_windows_begin.restype = C.c_int
+        lib.pp_windows_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+        lib.pp_windows_step.restype = C.c_int
+        lib.pp_windows_end.argtypes = [vp, _dp, _dp, _dp, C.POINTER(C.c_int)]
+        lib.pp_windows_end.restype = C.c_int
         lib.pp_last_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.pp_last_stats.restype = C.c_int
@@ -200,22 +206,31 @@ def pp_sigma(ctx, Z, prec: int = PP_FP64, metric: bool = False):
 
 
 PP_METRIC_NOALLOC_MAX_ELEMS = 1 << 19
+PP_METRIC_NOALLOC_MAX_NVEC = 32767
 
 
-def pp_metric_noalloc(ctx, Z, out):
+def pp_metric_noalloc(ctx, Z, out, nocc: int, nvir: int):
     """out = Sigma z without any device allocation in the library.
 
-    Z and out are CUDA float64 tensors [nvec, 2, nocc, nvir] that the caller owns
-    (nothing is allocated here either); nvec * nocc * nvir <= PP_METRIC_NOALLOC_MAX_ELEMS.
-    Calls that overlap in time on one device share the library's fixed scratch array
-    and must be serialised by the caller.
+    Z and out are CUDA float64 tensors [nvec, 2, nocc, nvir] on the current device (the
+    context's device) that the caller owns (nothing is allocated here either);
+    nvec * nocc * nvir <= PP_METRIC_NOALLOC_MAX_ELEMS and nvec <= PP_METRIC_NOALLOC_MAX_NVEC.
+    The C side cannot see shapes or devices, so they are checked here before the call: a
+    mis-shaped tensor would make the kernels read and write past its end.  Calls that
+    overlap in time on one device share the library's fixed scratch array and must be
+    serialised by the caller.
     """
     lib = load()
     import torch
 
+    dev = torch.cuda.current_device()
     for t in (Z, out):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise TypeError("pp_metric_noalloc needs contiguous CUDA float64 tensors")
+        if t.device.index != dev:
+            raise ValueError(f"pp_metric_noalloc: tensor on cuda:{t.device.index}, current device is cuda:{dev}")
+        if t.dim() != 4 or tuple(t.shape[1:]) != (2, int(nocc), int(nvir)):
+            raise ValueError(f"pp_metric_noalloc: expected [nvec, 2, {nocc}, {nvir}], got {tuple(t.shape)}")
     if Z.shape != out.shape:
         raise ValueError("Z and out must have the same shape")
     st = lib.pp_metric_noalloc(ctx, int(Z.shape[0]), Z.data_ptr(), out.data_ptr())
@@ -274,6 +289,44 @@ def pp_solve_windows(ctx, omega0, delta, k, allow_notconv: bool = False):
     return out, st
 
 
+class WindowRun:
+    """pp_windows_begin / pp_windows_step / pp_windows_end: a batched window solve driven one
+    block iteration at a time."""
+
+    def __init__(self, ctx, omega0, delta, k):
+        self.ctx = ctx
+        self.omega0 = _f64(omega0)
+        self.delta = _f64(delta)
+        self.k = np.ascontiguousarray(k, dtype=np.int32)
+        self.nwin = self.omega0.size
+        _check(load().pp_windows_begin(ctx, self.nwin, _ptr(self.omega0), _ptr(self.delta),
+                                       self.k.ctypes.data_as(C.POINTER(C.c_int))), ctx)
+
+    def step(self):
+        """One iteration of every unfinished window: (unfinished, sigma supervectors, sigma calls)."""
+        un = C.c_int()
+        nv = C.c_longlong()
+        nc = C.c_int()
+        _check(load().pp_windows_step(self.ctx, C.byref(un), C.byref(nv), C.byref(nc)), self.ctx)
+        return un.value, nv.value, nc.value
+
+    def end(self, allow_notconv: bool = False):
+        tot = int(self.k.sum())
+        om = np.zeros(tot)
+        osc = np.zeros(tot)
+        res = np.zeros(tot)
+        nf = np.zeros(self.nwin, dtype=np.int32)
+        st = load().pp_windows_end(self.ctx, _ptr(om), _ptr(osc), _ptr(res), nf.ctypes.data_as(C.POINTER(C.c_int)))
+        if not (allow_notconv and st == PP_ENOTCONV):
+            _check(st, self.ctx)
+        out, off = [], 0
+        for w in range(self.nwin):
+            n = int(nf[w])
+            out.append(dict(omega=om[off:off + n], osc=osc[off:off + n], resid=res[off:off + n]))
+            off += int(self.k[w])
+        return out, st
+
+
 def pp_last_stats(ctx):
     lib = load()
     it = C.c_int()
@@ -322,7 +375,7 @@ class Dot:
         return pp_sigma(self.ctx, Z, prec, metric)
 
     def metric_noalloc(self, Z, out):
-        return pp_metric_noalloc(self.ctx, Z, out)
+        return pp_metric_noalloc(self.ctx, Z, out, self.nocc, self.nvir)
 
     def diagonal(self):
         return pp_diagonal(self.ctx, self.nocc, self.nvir)
@@ -332,6 +385,9 @@ class Dot:
 
     def solve_windows(self, omega0, delta, k, **kw):
         return pp_solve_windows(self.ctx, omega0, delta, k, **kw)
+
+    def windows(self, omega0, delta, k):
+        return WindowRun(self.ctx, omega0, delta, k)
 
     def stats(self):
         return pp_last_stats(self.ctx)
@@ -376,7 +432,7 @@ def pp_server_add_dot(srv, nocc: int, nvir: int, naux: int, eps, B, mu=None) -> 
     st = lib.pp_server_add_dot(srv, nocc, nvir, naux, _ptr(eps), B.ctypes.data_as(C.c_void_p), bdt,
                                _ptr(mu_a) if mu_a is not None else None, C.byref(did))
     if st != PP_OK:
-        raise PPError(st, "pp_server_add_dot failed")
+        raise PPError(st, lib.pp_server_last_error(srv).decode(errors="replace") or "pp_server_add_dot failed")
     return did.value
 
 

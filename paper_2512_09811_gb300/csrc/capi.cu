@@ -112,6 +112,7 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
   c->ov = (long long)nocc * nvir;
   c->opt = o;
   pp_status st = guarded(c, [&]() -> pp_status {
+    PP_CUDA(cudaGetDevice(&c->device));
     if (o.cuda_stream) {
       c->stream = (cudaStream_t)o.cuda_stream;
     } else {
@@ -270,6 +271,39 @@ extern "C" pp_status pp_solve_windows(pp_ctx *c, int nwin, const double *omega0,
   });
 }
 
+extern "C" pp_status pp_windows_begin(pp_ctx *c, int nwin, const double *omega0, const double *delta,
+                                      const int *k) {
+  if (!c) return PP_EINVAL;
+  if (nwin < 1 || !omega0 || !delta || !k) {
+    c->err = "pp_windows_begin: bad argument";
+    return PP_EINVAL;
+  }
+  for (int w = 0; w < nwin; ++w)
+    if (k[w] < 1 || !std::isfinite(omega0[w]) || !(delta[w] >= 0)) {
+      c->err = "pp_windows_begin: bad window";
+      return PP_EINVAL;
+    }
+  return guarded(c, [&]() -> pp_status { return windows_begin(c, nwin, omega0, delta, k); });
+}
+
+extern "C" pp_status pp_windows_step(pp_ctx *c, int *unfinished, long long *sigma_vectors, int *sigma_calls) {
+  if (!c) return PP_EINVAL;
+  return guarded(c, [&]() -> pp_status {
+    pp_status st = windows_step(c, unfinished, sigma_vectors, sigma_calls);
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return st;
+  });
+}
+
+extern "C" pp_status pp_windows_end(pp_ctx *c, double *omega, double *osc, double *resid, int *nfound) {
+  if (!c) return PP_EINVAL;
+  if (!omega || !osc || !resid || !nfound) {
+    c->err = "pp_windows_end: bad argument";
+    return PP_EINVAL;
+  }
+  return guarded(c, [&]() -> pp_status { return windows_end(c, omega, osc, resid, nfound); });
+}
+
 extern "C" pp_status pp_last_stats(const pp_ctx *c, int *iterations, long long *sigma_vectors,
                                    double *sigma_ms, double *solve_ms) {
   if (!c) return PP_EINVAL;
@@ -294,6 +328,7 @@ extern "C" void pp_destroy(pp_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   tc_destroy(c);
+  window_run_destroy(c);
   if (c->wb) window_batch_destroy(c->wb);
   c->wb = nullptr;
   DevBuf *bufs[] = {&c->eps, &c->gap, &c->Bov, &c->Boo, &c->Bvv, &c->BvvP, &c->BooT, &c->GB,

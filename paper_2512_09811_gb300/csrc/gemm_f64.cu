@@ -190,6 +190,10 @@ template <class T> static void gemm_launch(const GemmS<T> &g, cudaStream_t s, co
   PP_LAUNCH_CHECK(name);
 }
 void gemm_f64(const GemmF64 &g, cudaStream_t s) { gemm_launch(g, s, "k_gemm_f64"); }
+void gemm_f64_preload() {
+  cudaFuncAttributes fa;
+  PP_CUDA(cudaFuncGetAttributes(&fa, k_gemm<double>));
+}
 void gemm_f32(const GemmF32 &g, cudaStream_t s) { gemm_launch(g, s, "k_gemm_f32"); }
 
 void tslab_f64(const double *Bov, const double *eps, int o, int v, int Q, int i0, int ni, double *T,

@@ -20,8 +20,10 @@
 //
 // Set-up: the first call on each device (a call with nvec = 0 does only this) looks
 // the array's device address up with cudaGetSymbolAddress, with that device current,
-// and caches it.  The lookup can load the library's device code, so this first call
-// must come before any stream capture begins on that device.
+// caches it, and has the runtime load the two kernels a call launches.  This can load
+// the library's device code, so the first call must come before any stream capture
+// begins on that device; later calls load nothing.  The current device must be the
+// context's device (checked: PP_EINVAL otherwise).
 #include "pp_internal.h"
 
 #include <mutex>
@@ -45,8 +47,9 @@ __global__ void k_metric_noalloc(double *__restrict__ out, const double *__restr
                                  long long ov, long long total);
 
 // Address of the array on the current device, looked up once per device; the same
-// set-up step also has the runtime load this file's kernel, so that later calls load
-// nothing.
+// set-up step also has the runtime load this file's kernel and the FP64 GEMM kernel the
+// call launches (under lazy module loading either would otherwise be loaded, and may take
+// device memory, at its first launch), so that later calls load nothing.
 double *scratch_on_current_device() {
   int dev = -1;
   PP_CUDA(cudaGetDevice(&dev));
@@ -61,6 +64,7 @@ double *scratch_on_current_device() {
     e = cudaFuncGetAttributes(&fa, k_metric_noalloc);
     if (e != cudaSuccess)
       throw PPError(PP_ECUDA, std::string("pp_metric_noalloc: cudaFuncGetAttributes: ") + cudaGetErrorString(e));
+    gemm_f64_preload();
     g_scratch_addr[dev] = p;
   }
   return g_scratch_addr[dev];
@@ -89,6 +93,11 @@ extern "C" pp_status pp_metric_noalloc(pp_ctx *c, int nvec, const double *Z, dou
     return PP_EINVAL;
   }
   const long long ov = c->ov;
+  if (nvec > PP_METRIC_NOALLOC_MAX_NVEC) {
+    c->err = "pp_metric_noalloc: nvec = " + std::to_string(nvec) + " exceeds the limit of " +
+             std::to_string(PP_METRIC_NOALLOC_MAX_NVEC) + " supervectors per call (split the batch)";
+    return PP_EINVAL;
+  }
   if ((long long)nvec * ov > PP_METRIC_NOALLOC_MAX_ELEMS) {
     c->err = "pp_metric_noalloc: nvec * nocc * nvir = " + std::to_string((long long)nvec * ov) +
              " exceeds the fixed scratch limit of " + std::to_string((long long)PP_METRIC_NOALLOC_MAX_ELEMS) +
@@ -96,6 +105,15 @@ extern "C" pp_status pp_metric_noalloc(pp_ctx *c, int nvec, const double *Z, dou
     return PP_EINVAL;
   }
   try {
+    // the scratch array is looked up on the current device and the kernels launch on the
+    // context's stream: both must be the context's device
+    int dev = -1;
+    PP_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device) {
+      c->err = "pp_metric_noalloc: the current device (" + std::to_string(dev) +
+               ") is not the context's device (" + std::to_string(c->device) + ")";
+      return PP_EINVAL;
+    }
     double *scratch = scratch_on_current_device();
     if (nvec == 0) return PP_OK;
     const long long R = 2LL * nvec;

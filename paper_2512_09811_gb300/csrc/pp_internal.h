@@ -92,6 +92,9 @@ using GemmF64 = GemmS<double>;
 using GemmF32 = GemmS<float>;
 void gemm_f64(const GemmF64 &g, cudaStream_t s);
 void gemm_f32(const GemmF32 &g, cudaStream_t s);
+// has the runtime load the FP64 GEMM kernel on the current device now (lazy module loading
+// would otherwise load it, and may allocate for it, at its first launch)
+void gemm_f64_preload();
 
 // T slab in FP64: rows (i - i0, c) for i in [i0, i0+ni), columns (j, d):
 // T[(ii*v + c)*ov + j*v + d] = t_ij^cd = ((ci|dj) - (cj|di)) / (e_i + e_j - e_c - e_d)
@@ -110,6 +113,7 @@ struct TcPlan;  // opaque
 // window solver slots (solver.cu)
 // ---------------------------------------------------------------------------
 struct WindowBatch;  // opaque
+struct WindowRun;    // opaque: the slots and k of a pp_windows_begin batch
 struct WindowResult {
   int status = PP_OK;  // PP_OK or PP_ENOTCONV
   int iters = 0;
@@ -123,6 +127,7 @@ struct WindowResult {
 struct pp_ctx {
   int o = 0, v = 0, Q = 0, n = 0;
   long long ov = 0;
+  int device = 0;  // CUDA device current at pp_create; all of the context's memory lives there
   pp_options opt{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -143,6 +148,8 @@ struct pp_ctx {
 
   // window slots of the solver (lazily built, reused across pp_solve_window calls)
   WindowBatch *wb = nullptr;
+  // windows begun by pp_windows_begin and not yet collected by pp_windows_end
+  WindowRun *run = nullptr;
 
   // stats of the last solve
   int st_iters = 0;
@@ -184,5 +191,10 @@ size_t tc_plan_bytes(const pp_ctx *c);
 long long tc_workspace_bytes(const pp_ctx *c);
 size_t ctx_device_bytes(const pp_ctx *c);
 int window_batch_used(const WindowBatch *wb);
+// windows driven one block iteration at a time (solver.cu; C ABI pp_windows_*)
+pp_status windows_begin(pp_ctx *c, int nwin, const double *omega0, const double *delta, const int *k);
+pp_status windows_step(pp_ctx *c, int *unfinished, long long *sigma_vectors, int *sigma_calls);
+pp_status windows_end(pp_ctx *c, double *omega, double *osc, double *resid, int *nfound);
+void window_run_destroy(pp_ctx *c);
 // dispatch of one sigma application (solver and C ABI)
 void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec);

@@ -352,6 +352,12 @@ extern "C" pp_status pp_server_add_dot(pp_server *S, int nocc, int nvir, int nau
   }
   std::lock_guard<std::mutex> lk(S->mu);
   d->est = estimate_bytes(nocc, nvir, naux, S->opt, S->slots);
+  // a dot whose footprint alone exceeds the whole budget could never be admitted
+  if (d->est > S->budget) {
+    S->err = "pp_server_add_dot: estimated device footprint " + std::to_string(d->est) +
+             " bytes exceeds the serving budget of " + std::to_string(S->budget) + " bytes";
+    return PP_ENOMEM;
+  }
   *dot_id = (int)S->dots.size();
   S->dots.push_back(std::move(d));
   return PP_OK;

@@ -1220,6 +1220,7 @@ struct WindowBatch {
   int *iscratch = nullptr;
   bool log_on = false;
   long long steps = 0;
+  long long sigma_calls = 0;  // sigma batches applied (a step applies one per precision phase)
   bool refine = false;
   int prec0 = PP_FP64;
 
@@ -1381,6 +1382,7 @@ struct WindowBatch {
     PP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->st_sigma_ms += ms;
     c->st_sigvec += nv;
+    ++sigma_calls;
   }
 
   // results of a window from its last extraction (the selection rules of pp_solve_window)
@@ -1910,6 +1912,7 @@ int window_batch_used(const WindowBatch *wb) { return wb->used(); }
 pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const double *delta,
                              const int *kk, double *omega_out, double *osc_out, double *resid_out,
                              double *vecs_out, int *nfound) {
+  window_run_destroy(c);  // a batch begun by pp_windows_begin and not collected is abandoned
   c->st_iters = 0;
   c->st_sigvec = 0;
   c->st_sigma_ms = 0.0;
@@ -1943,5 +1946,77 @@ pp_status solve_windows_impl(pp_ctx *c, int nwin, const double *omega0, const do
     if (vecs_out && nf > 0) std::memcpy(vecs_out + base * L, r.vecs.data(), sizeof(double) * (size_t)nf * L);
     base += kk[w];
   }
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// a batch of windows driven one block iteration at a time (pp_windows_begin / step / end)
+// ---------------------------------------------------------------------------
+struct WindowRun {
+  std::vector<int> slot, k;
+  long long steps0 = 0;
+};
+
+void window_run_destroy(pp_ctx *c) {
+  if (!c->run) return;
+  if (c->wb)
+    for (int sl : c->run->slot) c->wb->take(sl);
+  delete c->run;
+  c->run = nullptr;
+}
+
+pp_status windows_begin(pp_ctx *c, int nwin, const double *omega0, const double *delta, const int *kk) {
+  window_run_destroy(c);
+  c->st_iters = 0;
+  c->st_sigvec = 0;
+  c->st_sigma_ms = 0.0;
+  WindowBatch *wb = window_batch(c, nwin, false);
+  WindowRun *r = new WindowRun();
+  c->run = r;
+  r->steps0 = wb->steps;
+  for (int w = 0; w < nwin; ++w) {
+    const int sl = wb->add(omega0[w], delta[w], kk[w]);
+    if (sl < 0) throw PPError(PP_ECUDA, "window slots exhausted");
+    r->slot.push_back(sl);
+    r->k.push_back(kk[w]);
+  }
+  return PP_OK;
+}
+
+pp_status windows_step(pp_ctx *c, int *unfinished, long long *sigma_vectors, int *sigma_calls) {
+  if (!c->run || !c->wb) throw PPError(PP_EINVAL, "pp_windows_step: no windows begun");
+  WindowBatch *wb = c->wb;
+  const long long v0 = c->st_sigvec, k0 = wb->sigma_calls;
+  if (wb->has_work()) wb->step();
+  c->st_iters = (int)(wb->steps - c->run->steps0);
+  int n = 0;
+  for (int sl : c->run->slot) n += wb->finished(sl) ? 0 : 1;
+  if (unfinished) *unfinished = n;
+  if (sigma_vectors) *sigma_vectors = c->st_sigvec - v0;
+  if (sigma_calls) *sigma_calls = (int)(wb->sigma_calls - k0);
+  return PP_OK;
+}
+
+pp_status windows_end(pp_ctx *c, double *omega_out, double *osc_out, double *resid_out, int *nfound) {
+  if (!c->run || !c->wb) throw PPError(PP_EINVAL, "pp_windows_end: no windows begun");
+  WindowRun *r = c->run;
+  for (int sl : r->slot)
+    if (!c->wb->finished(sl)) throw PPError(PP_EINVAL, "pp_windows_end: windows still running (step until none is unfinished)");
+  pp_status st = PP_OK;
+  long long base = 0;
+  for (size_t w = 0; w < r->slot.size(); ++w) {
+    WindowResult res = c->wb->take(r->slot[w]);
+    if (res.status != PP_OK) st = (pp_status)res.status;
+    const int nf = (int)res.omega.size();
+    nfound[w] = nf;
+    for (int t = 0; t < nf; ++t) {
+      omega_out[base + t] = res.omega[t];
+      osc_out[base + t] = res.osc[t];
+      resid_out[base + t] = res.resid[t];
+    }
+    base += r->k[w];
+  }
+  delete r;
+  c->run = nullptr;
   return st;
 }

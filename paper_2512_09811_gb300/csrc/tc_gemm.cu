@@ -394,8 +394,10 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 256);
   // the virtual orbital energies of this CTA's d tile, for the denominators of the epilogue
-  __shared__ double eps_d[BM];
-  eps_d[threadIdx.x] = (d0 + (int)threadIdx.x < v) ? args.eps[args.o + d0 + threadIdx.x] : 0.0;
+  // (FP32: this part issues FP64 at a small fraction of its FP32 rate, and the relative
+  // error ~1e-7 of an FP32 denominator is far below the output's rounding)
+  __shared__ float eps_d[BM];
+  eps_d[threadIdx.x] = (d0 + (int)threadIdx.x < v) ? (float)args.eps[args.o + d0 + threadIdx.x] : 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
     const int c = c0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     const int o = args.o;
-    const double eij_c = (c < v) ? args.eps[i] + args.eps[j] - args.eps[o + c] : 0.0;
+    const float eij_c = (c < v) ? (float)(args.eps[i] + args.eps[j] - args.eps[o + c]) : 1.f;
     __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + c) * args.ldT + (long long)j * v;
     __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + c) * args.ldT + (long long)j * v : nullptr;
     float *frow = args.Tf ? args.Tf + ((long long)ii * v + c) * args.ldf + (long long)j * v : nullptr;
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
       if (c < v && vec && d0 + cc + 32 <= v) {
         float t[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) t[q] = (d1[q] - d2[q]) / (float)(eij_c - eps_d[cc + q]);
+        for (int q = 0; q < 32; ++q) t[q] = __fdividef(d1[q] - d2[q], eij_c - eps_d[cc + q]);
         const int dbase = d0 + cc;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
         for (int q = 0; q < 32; ++q) {
           const int d = d0 + cc + q;
           if (d < v) {
-            const float t = (d1[q] - d2[q]) / (float)(eij_c - eps_d[cc + q]);
+            const float t = __fdividef(d1[q] - d2[q], eij_c - eps_d[cc + q]);
             const __nv_bfloat16 h = __float2bfloat16_rn(t);
             hrow[d] = h;
             if (lrow) lrow[d] = __float2bfloat16_rn(t - __bfloat162float(h));
@@ -505,6 +507,291 @@ __global__ void __launch_bounds__(128, 1) k_tgen(const __grid_constant__ TgenMap
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// amplitude slab, persistent form used by the sigma product.
+//
+// The exchange integral of t_ij^cd is the direct integral of t_ij^dc, so the amplitudes
+// are antisymmetric in (c, d): t_ij^dc = -t_ij^cd.  One work item is an (i, j) pair and an
+// unordered pair of 128-wide virtual tiles (ct <= dt).  Its two accumulators are
+//   D1[c][d] = sum_Q B_Qic B_Qjd,   D2[c][d] = sum_Q B_Qjc B_Qid      (c in ct, d in dt),
+// t[c][d] = (D1 - D2)[c][d] / (e_i + e_j - e_c - e_d) is written as tile (ct, dt), and for
+// ct < dt its negated transpose as tile (dt, ct) -- through shared memory, so that every
+// row still leaves in 16-byte stores.  Half of the off-diagonal tile products of the
+// two-accumulator-per-tile form are saved.
+//
+// Warp roles (192 threads, one CTA per SM, persistent over the items):
+//   warp 0 lane 0  TMA producer, 2-stage ring of the four 128 x 64 operand tiles;
+//   warp 1 lane 0  MMA issuer; two TMEM accumulator pairs (512 columns), so the epilogue
+//                  of one item overlaps the main loop of the next;
+//   warps 2-5      epilogue (warp w reads TMEM lanes 32 (w % 4) ...): denominators in FP32
+//                  (relative error ~1e-7, far below the BF16 and BF16-pair roundings),
+//                  BF16 (pair) stores of tile (ct, dt), the transposed tile via shared memory.
+// Every mbarrier wait is bounded; after a timeout the CTA sets the error flag, skips the
+// remaining work (the epilogue warps still pass the same named barriers) and frees TMEM.
+// ---------------------------------------------------------------------------
+struct TgenPArgs {
+  int o, v, nk, i0, ni, nt, npairs, nseg;
+  long long nitems;          // ni * o * npairs
+  const float *eps;          // orbital energies (FP32 copy)
+  __nv_bfloat16 *Thi, *Tlo;  // Tlo may be null (BF16 form)
+  long long ldT;
+  int *err;
+};
+constexpr int TGP_STAGES = 2;
+constexpr uint32_t TGP_TILE = BM * BK * 2, TGP_STAGE = 4 * TGP_TILE;
+constexpr int TGP_XLD = 132;  // words per row of the transpose buffer (128 + 4: conflict-free)
+constexpr size_t tgenp_smem() { return (size_t)TGP_STAGES * TGP_STAGE + (size_t)BM * TGP_XLD * 4 + 1024; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// item -> (ii, j, ct, dt), pairs enumerated row by row of the upper triangle ct <= dt
+__device__ __forceinline__ void tgp_item(const TgenPArgs &a, long long item, int &ii, int &j, int &ct, int &dt) {
+  const int p = (int)(item % a.npairs);
+  const long long ij = item / a.npairs;
+  j = (int)(ij % a.o);
+  ii = (int)(ij / a.o);
+  int r = 0, rem = p;
+  while (rem >= a.nt - r) {
+    rem -= a.nt - r;
+    ++r;
+  }
+  ct = r;
+  dt = r + rem;
+}
+
+__global__ void __launch_bounds__(192, 1) k_tgen_p(const __grid_constant__ TgenMaps maps, TgenPArgs args) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint32_t *xbuf = reinterpret_cast<uint32_t *>(smem + TGP_STAGES * TGP_STAGE);
+  __shared__ __align__(8) uint64_t full_bar[TGP_STAGES], empty_bar[TGP_STAGES], accf[2], acce[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float eps_s[BM];
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TGP_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int steps = args.nk * args.nseg;
+  const int v = args.v, o = args.o;
+  if (warp == 0) {
+    if (lane == 0) {
+      long long kb = 0;
+      for (long long item = blockIdx.x; item < args.nitems && !abort_flag; item += gridDim.x) {
+        int ii, j, ct, dt;
+        tgp_item(args, item, ii, j, ct, dt);
+        const int i = args.i0 + ii, c0 = ct * BM, d0 = dt * BM;
+        for (int st = 0; st < steps; ++st, ++kb) {
+          const int s = (int)(kb % TGP_STAGES);
+          const uint32_t ph = (uint32_t)((kb / TGP_STAGES) & 1);
+          if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
+            atomicExch(args.err, 21);
+            abort_flag = 1;
+            break;
+          }
+          // segment 0: hi x hi, 1: hi x lo, 2: lo x hi
+          const int seg = st / args.nk, x = (st % args.nk) * BK;
+          const CUtensorMap *ma = (seg == 2) ? &maps.lo : &maps.hi;
+          const CUtensorMap *mb = (seg == 1) ? &maps.lo : &maps.hi;
+          uint8_t *sa = smem + s * TGP_STAGE;
+          mbar_expect_tx(&full_bar[s], TGP_STAGE);
+          tma_load_2d(sa, ma, x, i * v + c0, &full_bar[s]);                 // B_i[ct]
+          tma_load_2d(sa + TGP_TILE, mb, x, j * v + d0, &full_bar[s]);      // B_j[dt]
+          tma_load_2d(sa + 2 * TGP_TILE, ma, x, j * v + c0, &full_bar[s]);  // B_j[ct]
+          tma_load_2d(sa + 3 * TGP_TILE, mb, x, i * v + d0, &full_bar[s]);  // B_i[dt]
+        }
+      }
+      // before the CTA can exit, every load it issued must have landed (bounded waits)
+      for (long long k2 = kb > TGP_STAGES ? kb - TGP_STAGES : 0; k2 < kb; ++k2)
+        mbar_wait(&full_bar[k2 % TGP_STAGES], (uint32_t)((k2 / TGP_STAGES) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BM);
+      long long kb = 0;
+      int it = 0;
+      for (long long item = blockIdx.x; item < args.nitems && !abort_flag; item += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(&acce[b], (use & 1) ^ 1)) {
+          atomicExch(args.err, 22);
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d1 = tmem + b * 256, d2 = d1 + BM;
+        bool ok = true;
+        for (int st = 0; st < steps; ++st, ++kb) {
+          const int s = (int)(kb % TGP_STAGES);
+          const uint32_t ph = (uint32_t)((kb / TGP_STAGES) & 1);
+          if (!mbar_wait(&full_bar[s], ph)) {
+            atomicExch(args.err, 23);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint8_t *sa = smem + s * TGP_STAGE;
+          const uint64_t a1 = sdesc(sa), b1 = sdesc(sa + TGP_TILE), a2 = sdesc(sa + 2 * TGP_TILE),
+                         b2 = sdesc(sa + 3 * TGP_TILE);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t acc = (st > 0 || k > 0) ? 1u : 0u;
+            mma_bf16(d1, a1 + 2 * k, b1 + 2 * k, idesc, acc);
+            mma_bf16(d2, a2 + 2 * k, b2 + 2 * k, idesc, acc);
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        mma_commit(&accf[b]);
+      }
+      // every MMA issued has completed before TMEM is freed (bounded wait)
+      mma_commit(&done_bar);
+      mbar_wait(&done_bar, 0);
+    }
+    __syncwarp();
+  } else {
+    // epilogue: 128 threads; TMEM lane quarter q = warp % 4, tile row r = 32 q + lane
+    const int et = threadIdx.x - 64;  // 0..127
+    const int q = warp & 3, r = 32 * q + lane;
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    const bool vec = (v % 8) == 0 && (args.ldT % 8) == 0;
+    int it = 0;
+    for (long long item = blockIdx.x; item < args.nitems; item += gridDim.x, ++it) {
+      int ii, j, ct, dt;
+      tgp_item(args, item, ii, j, ct, dt);
+      const int i = args.i0 + ii, c0 = ct * BM, d0 = dt * BM;
+      const int b = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      const bool xpose = ct != dt;
+      epi_bar();  // the previous item's readers of eps_s and of the transpose buffer are done
+      eps_s[et] = (d0 + et < v) ? args.eps[o + d0 + et] : 0.f;
+      epi_bar();
+      bool ok = __all_sync(0xffffffffu, !abort_flag);
+      if (ok && !mbar_wait(&accf[b], use & 1)) {
+        if (lane == 0) atomicExch(args.err, 24);
+        abort_flag = 1;
+        ok = false;
+      }
+      ok = __all_sync(0xffffffffu, ok);  // warp-uniform: tcgen05.ld is a warp-wide instruction
+      tc_fence_after();
+      const int c = c0 + r;
+      if (ok) {
+        const float eij_c = (c < v) ? (float)((double)args.eps[i] + (double)args.eps[j] - (double)args.eps[o + c]) : 1.f;
+        __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + c) * args.ldT + (long long)j * v;
+        __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + c) * args.ldT + (long long)j * v : nullptr;
+        const uint32_t t1 = tmem + lane_off + b * 256, t2 = t1 + BM;
+        for (int cc = 0; cc < BM; cc += 32) {
+          float a1[32], a2[32];
+          tmem_ld32(t1 + cc, a1);
+          tmem_ld32(t2 + cc, a2);
+          uint32_t hw[16], lw[16];
+#pragma unroll
+          for (int q2 = 0; q2 < 16; ++q2) {
+            const float x0 = __fdividef(a1[2 * q2] - a2[2 * q2], eij_c - eps_s[cc + 2 * q2]);
+            const float x1 = __fdividef(a1[2 * q2 + 1] - a2[2 * q2 + 1], eij_c - eps_s[cc + 2 * q2 + 1]);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            hw[q2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[q2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          if (c < v) {
+            const int dbase = d0 + cc;
+            if (vec && dbase + 32 <= v) {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                *reinterpret_cast<uint4 *>(hrow + dbase + 8 * g) =
+                    make_uint4(hw[4 * g], hw[4 * g + 1], hw[4 * g + 2], hw[4 * g + 3]);
+                if (lrow)
+                  *reinterpret_cast<uint4 *>(lrow + dbase + 8 * g) =
+                      make_uint4(lw[4 * g], lw[4 * g + 1], lw[4 * g + 2], lw[4 * g + 3]);
+              }
+            } else {
+#pragma unroll
+              for (int q2 = 0; q2 < 32; ++q2) {
+                if (dbase + q2 < v) {
+                  const uint32_t h = (q2 & 1) ? (hw[q2 >> 1] >> 16) : (hw[q2 >> 1] & 0xffffu);
+                  const uint32_t l = (q2 & 1) ? (lw[q2 >> 1] >> 16) : (lw[q2 >> 1] & 0xffffu);
+                  hrow[dbase + q2] = __ushort_as_bfloat16((unsigned short)h);
+                  if (lrow) lrow[dbase + q2] = __ushort_as_bfloat16((unsigned short)l);
+                }
+              }
+            }
+          }
+          if (xpose) {  // word (hi | lo << 16) of t[c][d] at xbuf[d_local][c_local]
+#pragma unroll
+            for (int q2 = 0; q2 < 32; ++q2) {
+              const uint32_t h = (q2 & 1) ? (hw[q2 >> 1] >> 16) : (hw[q2 >> 1] & 0xffffu);
+              const uint32_t l = (q2 & 1) ? (lw[q2 >> 1] >> 16) : (lw[q2 >> 1] & 0xffffu);
+              xbuf[(cc + q2) * TGP_XLD + r] = h | (l << 16);
+            }
+          }
+        }
+      }
+      // hand the accumulator pair back to the MMA issuer
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+      if (xpose) {
+        epi_bar();
+        // thread et writes row d = d0 + et of tile (dt, ct): T[(ii, d)][(j, c)] = -t[c][d]
+        const int d = d0 + et;
+        if (ok && d < v) {
+          __nv_bfloat16 *hrow = args.Thi + ((long long)ii * v + d) * args.ldT + (long long)j * v;
+          __nv_bfloat16 *lrow = args.Tlo ? args.Tlo + ((long long)ii * v + d) * args.ldT + (long long)j * v : nullptr;
+          const uint32_t *xr = xbuf + et * TGP_XLD;
+          for (int g = 0; g < BM / 8; ++g) {
+            const int cb = c0 + 8 * g;
+            if (cb >= v) break;
+            const uint4 w0 = *reinterpret_cast<const uint4 *>(xr + 8 * g);
+            const uint4 w1 = *reinterpret_cast<const uint4 *>(xr + 8 * g + 4);
+            const uint32_t ws[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            if (vec && cb + 8 <= v) {
+              uint32_t hh[4], ll[4];
+#pragma unroll
+              for (int p2 = 0; p2 < 4; ++p2) {
+                hh[p2] = __byte_perm(ws[2 * p2], ws[2 * p2 + 1], 0x5410) ^ 0x80008000u;
+                ll[p2] = __byte_perm(ws[2 * p2], ws[2 * p2 + 1], 0x7632) ^ 0x80008000u;
+              }
+              *reinterpret_cast<uint4 *>(hrow + cb) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+              if (lrow) *reinterpret_cast<uint4 *>(lrow + cb) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+            } else {
+#pragma unroll
+              for (int p2 = 0; p2 < 8; ++p2) {
+                if (cb + p2 < v) {
+                  hrow[cb + p2] = __ushort_as_bfloat16((unsigned short)((ws[p2] & 0xffffu) ^ 0x8000u));
+                  if (lrow) lrow[cb + p2] = __ushort_as_bfloat16((unsigned short)((ws[p2] >> 16) ^ 0x8000u));
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -725,6 +1012,41 @@ void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq
   dim3 grid(nt * nt, o, ni);
   k_tgen<TGEN_STAGES><<<grid, 128, tgen_smem(), s>>>(maps, a);
   PP_LAUNCH_CHECK("k_tgen");
+}
+
+// persistent amplitude slab (sigma product): one CTA per SM over the (i, j, ct <= dt) items
+void tgen_p(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq, long long ov, int o, int v,
+            int i0, int ni, const float *eps, __nv_bfloat16 *Thi, __nv_bfloat16 *Tlo, long long ldT, int *err,
+            cudaStream_t s, int nsm) {
+  static bool attr = false;
+  if (!attr) {
+    PP_CUDA(cudaFuncSetAttribute(k_tgen_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tgenp_smem()));
+    attr = true;
+  }
+  TgenMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  maps.hi = kmajor_map(bovT, ldq, ov, ldq, BM);
+  maps.lo = bovT_lo ? kmajor_map(bovT_lo, ldq, ov, ldq, BM) : maps.hi;
+  const int nt = (v + BM - 1) / BM;
+  TgenPArgs a;
+  a.o = o;
+  a.v = v;
+  a.nk = (int)(ldq / BK);
+  a.i0 = i0;
+  a.ni = ni;
+  a.nt = nt;
+  a.npairs = nt * (nt + 1) / 2;
+  a.nseg = bovT_lo ? 3 : 1;
+  a.nitems = (long long)ni * o * a.npairs;
+  a.eps = eps;
+  a.Thi = Thi;
+  a.Tlo = Tlo;
+  a.ldT = ldT;
+  a.err = err;
+  const long long grid = std::min<long long>(a.nitems, std::max(1, nsm));
+  if (grid <= 0) return;
+  k_tgen_p<<<(unsigned)grid, 192, tgenp_smem(), s>>>(maps, a);
+  PP_LAUNCH_CHECK("k_tgen_p");
 }
 
 }  // namespace tc
@@ -1255,12 +1577,12 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
           if (tlo) PP_CUDA(cudaMemset2DAsync(tlo + ov, ldT * 2, 0, (ldT - ov) * 2, rows, s));
         }
         prof_mark(p->prof, 1, s);
-        tc::tgen(p->bovT_hi.as<bf>(), split ? p->bovT_lo.as<bf>() : nullptr, p->ldq, ov, o, v, i0, ni,
-                 c->eps.as<double>(), thi, tlo, ldT, err, s);
+        tc::tgen_p(p->bovT_hi.as<bf>(), split ? p->bovT_lo.as<bf>() : nullptr, p->ldq, ov, o, v, i0, ni,
+                   p->f_eps.as<float>(), thi, tlo, ldT, err, s, p->nsm);
         prof_mark(p->prof, 1, s);
-        if (p->prof.on) {
-          p->prof.launches[1] += 1;
-          p->prof.flops[1] += 2.0 * 2.0 * (double)Q * (double)rows * (double)ov * nseg;
+        if (p->prof.on) {  // algorithmic: one Q-long product per amplitude (the exchange
+          p->prof.launches[1] += 1;  // integral of (c,d) is the direct one of (d,c)), split counted once
+          p->prof.flops[1] += 2.0 * (double)Q * (double)rows * (double)ov;
         }
         // P = T C^T for this slab, written as BF16 pairs in two layouts:
         //   P1[r][i][c][q] (rows (r,i), K = (c,q)) and P2[r][c][i][q] (rows (r,c), K = (i,q))
@@ -1282,9 +1604,9 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         prof_mark(p->prof, 0, s);
         tc::gemm_bf16((int)rows, (int)NC, ldT, nseg, A, ldT, B, ldT, o1, err, s, &o2);
         prof_mark(p->prof, 0, s);
-        if (p->prof.on) {
-          p->prof.launches[0] += 1;
-          p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov * nseg;
+        if (p->prof.on) {  // algorithmic: the contraction once (the split form's three
+          p->prof.launches[0] += 1;  // products are an emulation of one)
+          p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov;
         }
       }
       // Bacc[(r,i)][a] += sum_(c,q) P1[(r,i)][(c,q)] Bvv[q][c][a]

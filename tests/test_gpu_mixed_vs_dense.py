@@ -88,3 +88,32 @@ def test_mixed_form_matches_dense(cuda_lib, case):
     assert st == pp.PP_OK
     for (w0, width, k), got in zip(wins, outs):
         _check(got, ref, w0, width, k, 1e-6, mixed=True)
+
+
+def test_stepped_windows_match_dense(cuda_lib, case):
+    """pp_windows_begin / step / end: the batched solve driven one block iteration at a time
+    reaches the same roots; collecting results while windows run is refused."""
+    pp = cuda_lib
+    inp, ref, wins = case
+    dot = pp.Dot(inp, prec=pp.PP_BF16, order=2, select=0, res_tol=1e-6, max_iter=300)
+    try:
+        run = dot.windows([w[0] for w in wins], [w[1] for w in wins], [w[2] for w in wins])
+        unfinished, nv, nc = run.step()
+        assert unfinished == len(wins) and nv > 0 and nc >= 1
+        with pytest.raises(pp.PPError) as ei:
+            run.end()
+        assert ei.value.status == pp.PP_EINVAL
+        steps = 1
+        while unfinished:
+            unfinished, nv, nc = run.step()
+            steps += 1
+            assert steps <= 400
+        assert run.step() == (0, 0, 0)  # nothing left to do
+        outs, st = run.end()
+        assert dot.stats()["iterations"] == steps
+    finally:
+        dot.close()
+    assert st == pp.PP_OK
+    for (w0, width, k), got in zip(wins, outs):
+        assert np.all(got["resid"] <= 1e-6)
+        _check(got, ref, w0, width, k, 1e-6, mixed=True)

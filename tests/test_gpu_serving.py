@@ -76,10 +76,30 @@ def test_serving_mix_matches_alone(dots_and_requests):
     assert stats["max_windows_per_step"] >= 2  # windows of different requests shared a step
 
 
+def _min_budget(pp, inp, slots, **opts):
+    """Smallest budget (to 1 MiB) at which the server admits this dot (add_dot refuses a dot
+    whose estimated footprint alone exceeds the budget with PP_ENOMEM)."""
+    lo, hi = 1 << 20, 1 << 40
+    while hi - lo > (1 << 20):
+        mid = (lo + hi) // 2
+        srv = pp.Server(mid, slots_per_dot=slots, nworkers=1, **opts)
+        try:
+            srv.add_dot(inp)
+            hi = mid
+        except pp.PPError as e:
+            assert e.status == pp.PP_ENOMEM
+            lo = mid
+        finally:
+            srv.close()
+    return hi
+
+
 def test_serving_evicts_when_over_budget(dots_and_requests):
-    """A 1-byte budget lets one dot be resident at a time: every switch evicts the idle one."""
+    """A budget that holds the larger dot but not both lets one dot be resident at a time:
+    every switch evicts the idle one."""
     pp, inps, reqs = dots_and_requests
-    out, stats = _run(pp, inps, reqs, budget=1, slots=2, workers=2)
+    budget = max(_min_budget(pp, inp, 2, prec=pp.PP_BF16, **OPTS) for inp in inps)
+    out, stats = _run(pp, inps, reqs, budget=budget, slots=2, workers=2)
     _compare(reqs, out)
     assert stats["completed"] == len(reqs)
     assert stats["ctx_evicted"] >= 1 and stats["ctx_created"] >= 2
@@ -98,5 +118,19 @@ def test_serving_rejects_bad_requests(cuda_lib):
             srv.submit(did, 1.0, 0.1, 0)
         with pytest.raises(pp.PPError):
             srv.submit(did, 1.0, -0.1, 4)  # negative width
+    finally:
+        srv.close()
+
+
+def test_serving_refuses_dot_beyond_budget(cuda_lib):
+    """Admission by footprint: a dot that cannot fit the whole budget is refused (PP_ENOMEM)."""
+    pp = cuda_lib
+    inp = make_inputs(16, 64, 192, seed=4, mode="perturbative")
+    srv = pp.Server(1 << 20, prec=pp.PP_BF16, **OPTS)
+    try:
+        with pytest.raises(pp.PPError) as ei:
+            srv.add_dot(inp)
+        assert ei.value.status == pp.PP_ENOMEM
+        assert "exceeds the serving budget" in ei.value.args[0]
     finally:
         srv.close()
