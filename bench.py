@@ -1,19 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark of the window solve: converged roots per second on one GB300.
+"""Benchmark of the batched window solver on one GB300.
 
-Workload (the configuration the metric is quoted on): one synthetic dot with
-nocc = 64, nvir = 256, naux = 768 (particle-hole dimension 16384), seed 1,
-perturbative-width density-fitting tensor; one window [omega0, omega0 + 0.1 Ha]
-with omega0 at the 20th percentile of diag(A)/diag(S); the k = 8 lowest roots,
-second order, mixed precision (BF16 tensor-core sigma, FP64 Krylov/Ritz,
-split-BF16 refinement to a residual of 1e-6).
+Workload (default, the batched block-Krylov configuration): one synthetic dot with
+nocc = 128, nvir = 512, naux = 1536 (particle-hole dimension 65536), seed 2, FP32 density-
+fitting tensor of perturbative width; 8 consecutive windows of 0.05 Ha from the 20th
+percentile of diag(A)/diag(S), the k = 8 lowest roots of each, block of 16 trial vectors
+per window; second order, mixed precision (BF16 tensor-core sigma with FP32 accumulation,
+FP64 Krylov basis and projected problems, split-BF16 refinement to a residual of 1e-6).
 
-A step is one full window solve (pp_solve_window) on device-resident inputs.
-value = roots converged / timed seconds; e2e repeats the step through the C ABI
-from host buffers (pp_create with the host B tensor, solve, results to host,
-pp_destroy) with the copies inside the timed region.
+A step is one block iteration of the 8-window batch: the whole hot path once -- Rayleigh-
+Ritz and the folded extraction, residuals, weighted-Jacobi directions, block CGS2, and one
+sigma batch per precision phase of every window's new vectors (pp_windows_step).  value =
+algorithmic sigma TFLOP/s of the timed steps (each contraction counted once; the split
+form's three products count as one); the full solve continues after the timed steps, and
+its converged roots per second are reported beside the value.  e2e repeats the whole solve
+through the C ABI from pinned host buffers (pp_create with the host B tensor, solve,
+results to host) with the copies inside the timed region.
 
-Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 """
 
 from __future__ import annotations
@@ -21,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,13 +38,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="dot-64x256x768", nocc=64, nvir=256, naux=768, seed=1, mode="perturbative",
-                pct=20.0, delta=0.1, k=8, order=2)
-METRIC = "converged roots/s"
+WORKLOADS = {
+    # 8 windows x k = 8, block 16 per window (128 trial supervectors per iteration)
+    "batched-128x512x1536": dict(nocc=128, nvir=512, naux=1536, seed=2, mode="perturbative", pct=20.0, nwin=8,
+                                 delta=0.05, k=8, block=16, order=2),
+    # one window, k = 8 (the plain-vs-mixed comparison)
+    "dot-64x256x768": dict(nocc=64, nvir=256, naux=768, seed=1, mode="perturbative", pct=20.0, nwin=1, delta=0.1,
+                           k=8, block=8, order=2),
+    # 4 windows x k = 16 (the large dot; a block iteration takes tens of seconds)
+    "dot-256x1024x3072": dict(nocc=256, nvir=1024, naux=3072, seed=4, mode="perturbative", pct=20.0, nwin=4,
+                              delta=0.05, k=16, block=16, order=2),
+}
+DEFAULT_WORKLOAD = "batched-128x512x1536"
+METRIC = "converged roots/s & sigma TFLOP/s at <=1e-6 Ha vs FP64 oracle; p50/p99 window latency"
 # residual |M x - theta Sigma x| / |x^T Sigma x| at which a root counts as converged; the split-
-# BF16 refinement reaches it, and the root then lies within |r|^2 / gap (<= 1e-6 Ha) of theta
+# BF16 refinement reaches it, and an isolated root then lies within |r|^2 / gap of theta
 RES_TOL = 1e-6
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# the oracle's bounded sample (its matrix-free sigma at the serving dot; see cpu_sample)
+ORACLE_SAMPLE = dict(nocc=32, nvir=128, naux=384, seed=3, mode="perturbative")
 
 
 def peaks():
@@ -120,16 +137,16 @@ def dist_setup():
     return world, rank, local
 
 
-def reduce_over_ranks(dist, ms: float, roots: float, device):
-    """Weak scaling: the job's time is the slowest rank's, its roots the sum over ranks."""
+def reduce_over_ranks(dist, ms: float, amount: float, device):
+    """Weak scaling: the job's time is the slowest rank's, its work the sum over ranks."""
     import torch
 
     ms_t = torch.tensor([float(ms)], device=device)
-    roots_t = torch.tensor([float(roots)], device=device)
+    am_t = torch.tensor([float(amount)], device=device)
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(roots_t, op=dist.ReduceOp.SUM)
-    return float(ms_t.item()), float(roots_t.item())
+        dist.all_reduce(am_t, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(am_t.item())
 
 
 def window_for_rank(omega0: float, delta: float, rank: int) -> float:
@@ -137,30 +154,36 @@ def window_for_rank(omega0: float, delta: float, rank: int) -> float:
     return omega0 + rank * delta
 
 
-def make_dot_inputs():
+def windows_for_rank(omega0: float, delta: float, nwin: int, rank: int):
+    """The nwin consecutive windows of this rank (replicas solve disjoint frequency ranges)."""
+    return [window_for_rank(omega0, delta, rank * nwin + w) for w in range(nwin)]
+
+
+def make_dot_inputs(w, b_dtype=np.float32):
     from synth.inputs import make_inputs
 
-    w = WORKLOAD
-    return make_inputs(w["nocc"], w["nvir"], w["naux"], seed=w["seed"], mode=w["mode"])
+    return make_inputs(w["nocc"], w["nvir"], w["naux"], seed=w["seed"], mode=w["mode"], b_dtype=b_dtype)
 
 
-# DRAM bytes (read + write) of one slab-GEMM launch from an ncu capture of the bench dot
-# (profiles/k_gemm_bf16_dot-64x256x768_sigma8.md); the timed launches mix R and the split form,
-# so this is the traffic of the captured launch shape, next to its algorithmic minimum
-SLAB_GEMM_CAPTURE = dict(dram_bytes=880.2e6, algorithmic_bytes=570e6,
-                         launch="R = 16 half-vectors, BF16 phase: 2048 x 12288 x 16384 (8.25e11 FLOP)")
-
-
-def sigma_flops(o, v, Q, nvec):
-    """Algorithmic FLOPs of one sigma batch (nvec supervectors, both halves)."""
+def sigma_flops_per_vector(o, v, Q):
+    """Algorithmic FLOPs of sigma for one supervector (both halves), each contraction once:
+    J 4 Q ov; U = Boo_Q V and the exchange sum_(Q,b) U_Q Bvv_Q 2 Q o^2 v + 2 Q o v^2;
+    E, F and their contraction with [Bov + Gamma; Bov] 8 Q o^2 v; C_Q(V) = V Bvv_Q - U 2 Q o v^2;
+    the amplitude contraction P_Q = T C_Q(V) 2 (ov)^2 Q; sum_Q C_Q(P_Q) 2 Q o v^2 + 2 Q o^2 v;
+    the A(2) pair-sum products 4 (o^2 v + o v^2)."""
     ov = o * v
-    R = 2 * nvec
-    small = R * (4 * Q * ov + 2 * Q * o * v * v + 2 * Q * o * o * v + 2 * 2 * Q * o * o * v
-                 + 2 * 2 * Q * o * o * v + 2 * Q * o * o * v + 2 * Q * o * v * v + 2 * Q * o * o * v
-                 + 4 * (o * o * v + o * v * v))
-    ladder = 2.0 * ov * ov * Q * R
-    tgen = 2.0 * 2.0 * Q * ov * ov
-    return small + ladder + tgen
+    half = (4 * Q * ov + 12 * Q * o * o * v + 6 * Q * o * v * v + 4 * (o * o * v + o * v * v)
+            + 2.0 * ov * ov * Q)
+    return 2.0 * half
+
+
+def tgen_flops(o, v, Q):
+    """Regeneration of the amplitudes once per sigma batch: one Q-long product per t_ij^cd."""
+    return 2.0 * Q * (o * v) ** 2
+
+
+def step_flops(o, v, Q, nvec, ncalls):
+    return nvec * sigma_flops_per_vector(o, v, Q) + ncalls * tgen_flops(o, v, Q)
 
 
 def run_ours(args, world, rank, local):
@@ -176,124 +199,182 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     pp.load()
     stream = torch.cuda.current_stream()
-    inp = make_dot_inputs()
-    w = WORKLOAD
-    opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=8, refine=1,
-                  cuda_stream=stream.cuda_stream)
+    w = WORKLOADS[args.workload]
+    o, v, Q = w["nocc"], w["nvir"], w["naux"]
+    inp = make_dot_inputs(w)
+    opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"], refine=1,
+                  max_iter=300, cuda_stream=stream.cuda_stream)
     t0 = time.time()
     dot = pp.Dot(inp, **opt_kw)
+    torch.cuda.synchronize()
     create_s = time.time() - t0
     dA, dS = dot.diagonal()
-    # every rank solves its own window (independent problems: weak scaling, no collective)
-    omega0 = window_for_rank(float(np.percentile((dA / dS).ravel(), w["pct"])), w["delta"], rank)
+    omega0 = float(np.percentile((dA / dS).ravel(), w["pct"]))
+    wins = windows_for_rank(omega0, w["delta"], w["nwin"], rank)
+    deltas = [w["delta"]] * w["nwin"]
+    ks = [w["k"]] * w["nwin"]
 
-    def step():
-        return dot.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
+    # ---- the batched solve, one block iteration per step --------------------------------
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    run = dot.windows(wins, deltas, ks)
+    solves = []  # (roots converged, ms, iterations, sigma supervectors, max resid) per completed batch
+    cur = dict(ms=0.0, it=0, nv=0)
+
+    def one_step():
+        nonlocal run
+        ev0.record(stream)
+        un, nv, nc = run.step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        cur["ms"] += ms
+        cur["it"] += 1
+        cur["nv"] += nv
+        if un == 0:  # the batch is done: collect it and start the same windows again
+            res, st = run.end(allow_notconv=True)
+            roots = sum(int(np.count_nonzero(r["resid"] <= RES_TOL * 1.0000001)) for r in res)
+            mres = max((float(r["resid"].max()) for r in res if len(r["resid"])), default=None)
+            solves.append(dict(roots=roots, ms=cur["ms"], iterations=cur["it"], sigma_vectors=cur["nv"],
+                               max_resid=mres, status=int(st), found=[len(r["omega"]) for r in res]))
+            cur.update(ms=0.0, it=0, nv=0)
+            run = dot.windows(wins, deltas, ks)
+        return ms, step_flops(o, v, Q, nv, nc), nv
 
     for _ in range(max(args.warmup, 0)):
-        step()
+        one_step()
     pk = peaks()
-    roots = 0
-    iters = []
-    res_all = []
     pp.pp_profile(dot.ctx, True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     launches0 = pp.pp_kernel_launches()
+    timed_ms, timed_flops, timed_nv = 0.0, 0.0, 0
     with ClockSampler(local) as clk:
-        ev0.record(stream)
         for _ in range(args.steps):
-            out = step()
-            ok = out["resid"] <= RES_TOL * 1.0000001
-            roots += int(np.count_nonzero(ok))
-            res_all.extend(out["resid"].tolist())
-            iters.append(dot.stats()["iterations"])
-        ev1.record(stream)
+            ms, fl, nv = one_step()
+            timed_ms += ms
+            timed_flops += fl
+            timed_nv += nv
         torch.cuda.synchronize()
     launches = pp.pp_kernel_launches() - launches0
-    if dist is not None:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     k0 = pp.pp_profile_read(dot.ctx, 0)
     k1 = pp.pp_profile_read(dot.ctx, 1)
+    k2 = pp.pp_profile_read(dot.ctx, 2)
     pp.pp_profile(dot.ctx, False)
-    stats = dot.stats()
-    ms_max, roots_tot = reduce_over_ranks(dist, ms, roots, "cuda")
-    value = roots_tot / (ms_max / 1e3)
+    if dist is not None:
+        dist.barrier()
+    ms_max, flops_tot = reduce_over_ranks(dist, timed_ms, timed_flops, "cuda")
+    value = flops_tot / (ms_max / 1e3) / 1e12
+    # finish the solve that was running when the timed steps ended (at least one full batch)
+    while not solves:
+        one_step()
+    first = solves[0]
+    solve_ms_max, roots_tot = reduce_over_ranks(dist, first["ms"], first["roots"], "cuda")
+    roots_per_s = roots_tot / (solve_ms_max / 1e3)
+    solve_flops = first["sigma_vectors"] * sigma_flops_per_vector(o, v, Q)
 
-    # sigma throughput of one BF16 batch of 8 supervectors (device-resident, CUDA events)
-    from synth.inputs import random_vectors
-
-    Zh = random_vectors(8, w["nocc"], w["nvir"], seed=5)
-    Zd = torch.from_numpy(Zh).cuda()
-    for _ in range(2):
-        pp.pp_sigma(dot.ctx, Zd, prec=pp.PP_BF16)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    nrep = 3
-    for _ in range(nrep):
-        pp.pp_sigma(dot.ctx, Zd, prec=pp.PP_BF16)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sig_ms = e0.elapsed_time(e1) / nrep
-    sig_tflops = sigma_flops(w["nocc"], w["nvir"], w["naux"], 8) / (sig_ms / 1e3) / 1e12
-
-    # end to end through the C ABI from host buffers: create (B to the device), solve, results back
+    # ---- end to end through the C ABI from pinned host buffers ---------------------------
     from synth.inputs import DotInputs
 
-    # the host inputs in pinned memory
     pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(inp, f))).pin_memory().numpy() for f in ("eps", "B", "mu")}
     pinned = DotInputs(nocc=inp.nocc, nvir=inp.nvir, naux=inp.naux, sigma_b=inp.sigma_b, seed=inp.seed, **pin)
     h2d = inp.eps.nbytes + inp.B.nbytes + inp.mu.nbytes
-    d2h = w["k"] * 3 * 8
-    torch.cuda.synchronize()
-    t0 = time.time()
-    ee = 0
-    for _ in range(max(1, min(args.steps, 2))):
+    d2h = sum(ks) * 3 * 8 + 4 * len(ks)
+    e2e = None
+    if not args.no_e2e:
+        dot.close()
+        torch.cuda.synchronize()
+        t0 = time.time()
         d2 = pp.Dot(pinned, **opt_kw)
-        o2 = d2.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
-        ee += int(np.count_nonzero(o2["resid"] <= RES_TOL * 1.0000001))
+        outs, st2 = d2.solve_windows(wins, deltas, ks, allow_notconv=True)
+        stats2 = d2.stats()
+        torch.cuda.synchronize()
+        e2e_s = time.time() - t0
         d2.close()
-    torch.cuda.synchronize()
-    e2e_s = time.time() - t0
-    e2e_max, ee_tot = reduce_over_ranks(dist, e2e_s, ee, "cuda")
-    e2e_val = ee_tot / e2e_max
+        ee = sum(int(np.count_nonzero(r["resid"] <= RES_TOL * 1.0000001)) for r in outs)
+        e2e_fl = stats2["sigma_vectors"] * sigma_flops_per_vector(o, v, Q)
+        e2e_max, e2e_flops = reduce_over_ranks(dist, e2e_s * 1e3, e2e_fl, "cuda")
+        _, ee_tot = reduce_over_ranks(dist, e2e_s * 1e3, ee, "cuda")
+        e2e = dict(value=e2e_flops / (e2e_max / 1e3) / 1e12, unit="TFLOP/s", h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(d2h), step="pp_create from pinned host inputs + pp_solve_windows + "
+                   "results to host", roots_per_s=ee_tot / (e2e_max / 1e3), seconds=e2e_max / 1e3,
+                   iterations=stats2["iterations"])
+    else:
+        dot.close()
 
+    # ---- roofline of the dominant kernel: the amplitude-contraction GEMM -----------------
     achieved = (k0["flops"] / (k0["ms"] / 1e3) / 1e12) if k0["ms"] > 0 else None
+    hw = ((k0["flops"] + 2.0 * k2["flops"]) / (k0["ms"] / 1e3) / 1e12) if k0["ms"] > 0 else None
     peak = pk["bf16_sustained"]
-    cap = SLAB_GEMM_CAPTURE
-    roof = dict(bound="tensor", kernel="k_gemm_bf16 (amplitude contraction, tcgen05)",
-                achieved=achieved, peak=peak, unit="TFLOP/s",
-                frac=(achieved / peak) if achieved else None, traffic=cap["dram_bytes"],
-                traffic_launch=cap["launch"], traffic_algorithmic_bytes=cap["algorithmic_bytes"],
+    cap = SLAB_GEMM_CAPTURE.get(args.workload)
+    roof = dict(bound="tensor", kernel="k_gemm_bf16 amplitude contraction P_Q = T C_Q(V) (tcgen05)",
+                achieved=achieved, peak=peak, unit="TFLOP/s", frac=(achieved / peak) if achieved else None,
+                traffic=cap["dram_bytes"] if cap else None,
                 peak_source=f"{pk['src']} bf16 sustained", launches=k0["launches"],
                 avg_launch_ms=(k0["ms"] / k0["launches"]) if k0["launches"] else None,
-                tgen=dict(launches=k1["launches"], ms=k1["ms"],
-                          achieved=(k1["flops"] / (k1["ms"] / 1e3) / 1e12) if k1["ms"] > 0 else None))
+                hardware_mma_tflops=hw, hardware_frac=(hw / peak) if hw else None,
+                split_form_share_of_launch_flops=(k2["flops"] / k0["flops"]) if k0["flops"] else None,
+                generator=dict(kernel="k_tgen_p", launches=k1["launches"], ms=k1["ms"],
+                               achieved=(k1["flops"] / (k1["ms"] / 1e3) / 1e12) if k1["ms"] > 0 else None))
+    if cap:
+        roof.update(traffic_launch=cap["launch"], traffic_algorithmic_bytes=cap["algorithmic_bytes"])
     line = dict(
-        metric=METRIC, value=value, unit="roots/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=ms_max / max(args.steps, 1), higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="bf16", data="synthetic",
-        config=dict(workload=w["name"], nocc=w["nocc"], nvir=w["nvir"], naux=w["naux"], k=w["k"],
-                    window_ha=w["delta"], order=w["order"], precision="bf16 tensor cores + fp64 krylov + bf16x3 refine",
-                    inputs=w["mode"], l2="inputs larger than L2 (B tensor 630 MB fp64 resident)",
+        dtype="bf16 (fp32 accumulate; fp64 krylov)", data="synthetic",
+        config=dict(workload=args.workload, nocc=o, nvir=v, naux=Q, windows=w["nwin"], k=w["k"],
+                    window_ha=w["delta"], block=w["block"], order=w["order"],
+                    precision="bf16 tensor cores + fp64 krylov + bf16x3 refinement to 1e-6",
+                    inputs=w["mode"], step="one block iteration of all windows (pp_windows_step)",
+                    l2="inputs larger than L2 (FP32 B tensor %.1f GB; slab and operands > 129 MB)" % (inp.B.nbytes / 1e9),
                     parallelism=f"replicas{world}"),
+        roots=dict(roots_per_s=roots_per_s, roots=int(roots_tot), solve_s=solve_ms_max / 1e3,
+                   iterations=first["iterations"], sigma_vectors=first["sigma_vectors"],
+                   max_resid=first["max_resid"], found=first["found"], status=first["status"],
+                   sigma_tflops=solve_flops / (first["ms"] / 1e3) / 1e12),
         roofline=roof,
-        e2e=dict(value=e2e_val, unit="roots/s", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
+        e2e=e2e,
         gpu_launches=int(launches),
         clocks=clk.summary(),
-        extra=dict(create_s=create_s, iterations=iters, sigma_vectors=stats["sigma_vectors"],
-                   sigma_ms_last_solve=stats["sigma_ms"], solve_ms_last=stats["solve_ms"],
-                   max_resid=max(res_all) if res_all else None,
-                   sigma_batch8_ms=sig_ms, sigma_tflops=sig_tflops),
+        extra=dict(create_s=create_s, timed_sigma_vectors=timed_nv, omega0=omega0),
     )
-    dot.close()
     return line
+
+
+# DRAM bytes (read + write) per launch of the amplitude-contraction GEMM from an ncu capture
+SLAB_GEMM_CAPTURE = {}
+
+
+def mixed_vs_fp64_leg(args):
+    """The plain FP64 form against the mixed form on the same single window (64/256/768, k = 8,
+    residual 1e-6): converged roots/s of each, one full solve each on device-resident inputs."""
+    import torch
+
+    import paper_2512_09811_gb300 as pp
+
+    w = WORKLOADS["dot-64x256x768"]
+    inp = make_dot_inputs(w, b_dtype=np.float64)
+    out = {}
+    for name, prec in (("mixed", pp.PP_BF16), ("fp64", pp.PP_FP64)):
+        d = pp.Dot(inp, prec=prec, order=2, select=0, res_tol=RES_TOL, block=w["block"], max_iter=300)
+        dA, dS = d.diagonal()
+        w0 = float(np.percentile((dA / dS).ravel(), w["pct"]))
+        torch.cuda.synchronize()
+        t0 = time.time()
+        r = d.solve_window(w0, w["delta"], w["k"], allow_notconv=True)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        st = d.stats()
+        d.close()
+        n = int(np.count_nonzero(r["resid"] <= RES_TOL * 1.0000001))
+        out[name] = dict(roots=n, seconds=dt, roots_per_s=n / dt, iterations=st["iterations"],
+                         sigma_vectors=st["sigma_vectors"], omega=[float(x) for x in r["omega"]])
+    out["mixed_over_fp64"] = out["mixed"]["roots_per_s"] / out["fp64"]["roots_per_s"]
+    out["max_root_difference_ha"] = float(np.max(np.abs(np.array(out["mixed"]["omega"]) - np.array(out["fp64"]["omega"])))) \
+        if len(out["mixed"]["omega"]) == len(out["fp64"]["omega"]) else None
+    out["workload"] = "dot-64x256x768, one window [pct20, +0.1 Ha], k = 8, residual 1e-6"
+    return out
 
 
 SERVING_SIZES = [(32, 128, 384), (64, 256, 768), (128, 512, 1536)]
@@ -312,7 +393,8 @@ def serving_leg(args):
     pool = []  # (size index, inputs, sorted diag(A)/diag(S))
     for si, (o, v, Q) in enumerate(sizes):
         for di in range(4):
-            inp = make_inputs(o, v, Q, seed=3000 + 10 * si + di, mode="perturbative")
+            inp = make_inputs(o, v, Q, seed=3000 + 10 * si + di, mode="perturbative",
+                              b_dtype=np.float32 if o >= 128 else np.float64)
             d = pp.Dot(inp, **opts)
             dA, dS = d.diagonal()
             d.close()
@@ -337,107 +419,125 @@ def serving_leg(args):
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            rid.append((srv.submit(ids[dot], w0, width, k), k, ta))
+            rid.append((srv.submit(ids[dot], w0, width, k), k, ta, pool[dot][0]))
         lat, roots, finish, notconv = [], 0, 0.0, 0
-        for (r_id, k, ta) in rid:
-            out = srv.wait(r_id, k, timeout_ms=1_800_000, allow_notconv=True)
+        by_size = {si: [] for si in range(len(sizes))}
+        for (r_id, k, ta, si) in rid:
+            out = srv.wait(r_id, k, timeout_ms=3_600_000, allow_notconv=True)
             lat.append(out["latency_ms"])
+            by_size[si].append(out["latency_ms"])
             roots += int(np.count_nonzero(out["resid"] <= RES_TOL * 1.0000001))
             notconv += int(out["status"] != pp.PP_OK)
             finish = max(finish, ta + out["latency_ms"] / 1e3)
         st = srv.stats()
     finally:
         srv.close()
-    return dict(requests=n_req, arrival_rate_per_s=rate, sizes=[list(z) for z in sizes], dots_per_size=4,
-                k_choices=[4, 8, 16], window_ha=[0.05, 0.2], start="U[pct10, pct50] of diag(A)/diag(S)",
+    return dict(requests=n_req, arrival_rate_per_s=rate, arrivals_s=reqs[-1][0], sizes=[list(z) for z in sizes],
+                dots_per_size=4, k_choices=[4, 8, 16], window_ha=[0.05, 0.2],
+                start="U[pct10, pct50] of diag(A)/diag(S)",
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                p50_ms_by_size={str(list(sizes[s])): float(np.percentile(v_, 50)) for s, v_ in by_size.items() if v_},
+                p99_ms_by_size={str(list(sizes[s])): float(np.percentile(v_, 99)) for s, v_ in by_size.items() if v_},
                 roots_per_s=roots / finish, roots=roots, wall_s=finish, not_converged=notconv,
                 slots_per_dot=4, workers=4, max_concurrent_dots=st["max_concurrent_dots"],
                 max_windows_per_step=st["max_windows_per_step"], ctx_created=st["ctx_created"],
                 ctx_evicted=st["ctx_evicted"], failed=st["failed"])
 
 
+def host_cpu():
+    name = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return name
+
+
+def cpu_sample(nvec: int):
+    """The oracle as it stands (plain FP64 NumPy, OpenBLAS threads on every host core): its
+    matrix-free sigma of nvec supervectors at the 32/128/384 dot, the largest dot whose
+    oracle sigma takes a few seconds per supervector.  Returns (seconds, setup seconds,
+    algorithmic FLOPs of the sample, counted as for the GPU)."""
+    from oracle import pp_oracle as po
+    from synth.inputs import make_inputs, random_vectors
+
+    s = ORACLE_SAMPLE
+    inp = make_inputs(s["nocc"], s["nvir"], s["naux"], seed=s["seed"], mode=s["mode"])
+    t0 = time.time()
+    ref = po.SigmaRef(inp.eps, inp.B, inp.nocc, order=2)
+    setup = time.time() - t0
+    Z = random_vectors(nvec, s["nocc"], s["nvir"], seed=5)
+    return ref, Z, setup, step_flops(s["nocc"], s["nvir"], s["naux"], nvec, 1)
+
+
+def cpu_baseline_leg():
+    """Bounded oracle sample for the cpu_baseline field (rank 0, N = 1 only)."""
+    ref, Z, setup, fl = cpu_sample(4)
+    t0 = time.time()
+    ref.sigma(Z)
+    dt = time.time() - t0
+    return dict(value=fl / dt / 1e12, unit="TFLOP/s", cores=os.cpu_count(), cpu=host_cpu(), kind="oracle",
+                sample=f"oracle FP64 matrix-free sigma of 4 supervectors at the 32/128/384 dot ({dt:.2f} s, setup "
+                       f"{setup:.1f} s); algorithmic FLOPs counted as for the GPU")
+
+
 def run_reference(args, world, rank):
-    """The CPU oracle (plain FP64 NumPy) on this machine's host cores: its matrix-free sigma,
-    timed on one trial supervector per step, scaled by the sigma supervectors a window
-    solve needs."""
+    """The reference arm: the CPU oracle (plain FP64 NumPy) on this machine's host cores, each step
+    its matrix-free sigma of 2 supervectors at the 32/128/384 dot (a bounded sample: the oracle
+    cannot hold the 128/512/1536 amplitudes, 34 GB, nor finish one of its sigmas in minutes)."""
     if rank != 0:
         return None
-    from oracle import pp_oracle as po
-    from synth.inputs import random_vectors
-
-    inp = make_dot_inputs()
-    w = WORKLOAD
-    t0 = time.time()
-    ref = po.SigmaRef(inp.eps, inp.B, inp.nocc, order=w["order"])
-    setup_s = time.time() - t0
-    Z = random_vectors(1, w["nocc"], w["nvir"], seed=5)
-    ref.sigma(Z)  # warm caches
+    ref, Z, setup, fl = cpu_sample(2)
+    for _ in range(max(args.warmup, 0)):
+        ref.sigma(Z)
     times = []
     for _ in range(max(1, args.steps)):
         t0 = time.time()
         ref.sigma(Z)
         times.append(time.time() - t0)
-    t_vec = statistics.median(times)
-    vecs_per_root = REF_SIGMA_VECTORS_PER_ROOT
-    value = 1.0 / (t_vec * vecs_per_root)
+    tot = sum(times)
+    value = fl * len(times) / tot / 1e12
     cores = os.cpu_count()
-    sample = (f"oracle FP64 sigma of 1 supervector per step at {w['name']} (median {t_vec:.2f} s, "
-              f"setup {setup_s:.1f} s), times {vecs_per_root} supervectors per converged root")
-    return dict(metric=METRIC, value=value, unit="roots/s", n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=t_vec * 1e3, higher_is_better=True, scaling="weak",
+    sample = (f"oracle FP64 matrix-free sigma of 2 supervectors per step at the 32/128/384 dot (mean "
+              f"{tot / len(times):.2f} s per step, setup {setup:.1f} s); algorithmic FLOPs counted as for the GPU")
+    w = WORKLOADS[args.workload]
+    return dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=tot / len(times) * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=w["name"], nocc=w["nocc"], nvir=w["nvir"], naux=w["naux"], k=w["k"]),
-                cpu_baseline=dict(value=value, unit="roots/s", cores=cores, kind="oracle", sample=sample),
-                e2e=dict(value=value, unit="roots/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
-
-
-# sigma supervectors per converged root of the window solve at this workload: the GPU solver
-# needed 255-293 supervector products for the 8 roots of one window (bench and trace runs)
-REF_SIGMA_VECTORS_PER_ROOT = 33
-
-
-def cpu_baseline_leg():
-    """Bounded oracle sample for the cpu_baseline field (rank 0, N = 1 only)."""
-    from oracle import pp_oracle as po
-    from synth.inputs import random_vectors
-
-    inp = make_dot_inputs()
-    w = WORKLOAD
-    t0 = time.time()
-    ref = po.SigmaRef(inp.eps, inp.B, inp.nocc, order=w["order"])
-    setup = time.time() - t0
-    Z = random_vectors(1, w["nocc"], w["nvir"], seed=5)
-    t0 = time.time()
-    ref.sigma(Z)
-    t_vec = time.time() - t0
-    return dict(value=1.0 / (t_vec * REF_SIGMA_VECTORS_PER_ROOT), unit="roots/s", cores=os.cpu_count(),
-                kind="oracle",
-                sample=f"1 oracle FP64 sigma supervector at {w['name']} ({t_vec:.2f} s, setup {setup:.1f} s) "
-                       f"x {REF_SIGMA_VECTORS_PER_ROOT} supervectors per root")
+                config=dict(workload=args.workload, nocc=w["nocc"], nvir=w["nvir"], naux=w["naux"],
+                            windows=w["nwin"], k=w["k"], window_ha=w["delta"], block=w["block"], order=w["order"]),
+                cpu_baseline=dict(value=value, unit="TFLOP/s", cores=cores, cpu=host_cpu(), kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=value, unit="TFLOP/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
 def profile_workload(args):
-    """Small fixed workloads for ncu captures (no timing, no JSON line)."""
+    """Small fixed workloads for ncu captures (no timing, no JSON line).  The sigma workload
+    limits the tensor-core workspace (workspace_gb) so that the capture holds a few GB."""
     import torch
 
     import paper_2512_09811_gb300 as pp
     from synth.inputs import random_vectors
 
-    w = WORKLOAD
-    inp = make_dot_inputs()
+    w = WORKLOADS[args.workload]
+    inp = make_dot_inputs(w)
     if args.profile_sigma:
-        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"])
-        Z = torch.from_numpy(random_vectors(8, w["nocc"], w["nvir"], seed=5)).cuda()
-        for _ in range(2):
-            pp.pp_sigma(dot.ctx, Z, prec=pp.PP_BF16)
+        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], workspace_gb=args.profile_workspace_gb)
+        Z = torch.from_numpy(random_vectors(args.profile_sigma, w["nocc"], w["nvir"], seed=5)).cuda()
+        for prec in (pp.PP_BF16, pp.PP_BF16X3):
+            pp.pp_sigma(dot.ctx, Z, prec=prec)
         torch.cuda.synchronize()
     else:
-        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL,
+        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"],
                      max_iter=args.profile_solve)
         dA, dS = dot.diagonal()
         omega0 = float(np.percentile((dA / dS).ravel(), w["pct"]))
-        dot.solve_window(omega0, w["delta"], w["k"], allow_notconv=True)
+        dot.solve_windows(windows_for_rank(omega0, w["delta"], w["nwin"], 0), [w["delta"]] * w["nwin"],
+                          [w["k"]] * w["nwin"], allow_notconv=True)
     dot.close()
     print("profile workload done", flush=True)
 
@@ -445,19 +545,25 @@ def profile_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve from host buffers")
+    ap.add_argument("--fp64-leg", action="store_true",
+                    help="also solve the 64/256/768 window in the plain FP64 form and the mixed form "
+                         "(minutes: the FP64 form issues at GB300's FP64 rate)")
+    ap.add_argument("--serving", action="store_true", help="run the serving-trace leg")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-rate", type=float, default=50.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serving-all-sizes", action="store_true",
                     help="include 128/512/1536 dots in the serving mix (minutes per request)")
-    ap.add_argument("--profile-sigma", action="store_true",
-                    help="profiling workload: create the dot, two BF16 sigma batches of 8 supervectors")
+    ap.add_argument("--profile-sigma", type=int, default=0,
+                    help="profiling workload: create the dot, one BF16 and one split sigma of this many supervectors")
+    ap.add_argument("--profile-workspace-gb", type=float, default=2.0)
     ap.add_argument("--profile-solve", type=int, default=0,
-                    help="profiling workload: one window solve capped at this many iterations")
+                    help="profiling workload: the workload's windows solved with this iteration cap")
     args = ap.parse_args()
     if args.profile_sigma or args.profile_solve:
         profile_workload(args)
@@ -470,7 +576,9 @@ def main():
         return
     line = run_ours(args, world, rank, local)
     if rank == 0:
-        if world == 1 and not args.no_serving:
+        if world == 1 and args.fp64_leg:
+            line["mixed_vs_fp64"] = mixed_vs_fp64_leg(args)
+        if world == 1 and args.serving:
             line["serving"] = serving_leg(args)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()

@@ -88,6 +88,9 @@ typedef struct {
   double workspace_gb; /* device memory for one chunk of the tensor-core sigma workspaces
                           (0 = automatic: a quarter of the free memory at first use, between
                           12 and 64 GB) */
+  int tda;             /* 1: Tamm-Dancoff form (Sec. 2.2 with B = 0): M = diag(A, A), so the
+                          roots are those of A X = omega S X and the sigma products skip every
+                          B term (the amplitude contraction included); 0 (default): full form */
 } pp_options;
 
 /* Fill *opt with the defaults above. */
@@ -182,6 +185,41 @@ pp_status pp_solve_windows(pp_ctx *ctx, int nwin, const double *omega0, const do
                            const int *k, double *omega, double *osc, double *resid, int *nfound);
 
 /*
+ * Frequency-dependent linear response (Eq. pp_adc at real frequencies): the dipole
+ * polarizability tensor
+ *     alpha[f][c][c'] = F_c^T (M - omega_f Sigma)^-1 F_c',   F_c = (mu_c; mu_c),
+ * which equals sum_n 2 omega_n (mu_c . (X_n + Y_n)) (mu_c' . (X_n + Y_n)) / (omega_n^2 - omega_f^2)
+ * over the positive roots (so the trace / 3 is sum_n f_n / (omega_n^2 - omega_f^2)).  The
+ * three systems per frequency are solved by preconditioned MINRES with the Jacobi diagonal
+ * |diag(M - omega Sigma)| (floored at jacobi_floor) as preconditioner; mixed contexts refine
+ * on the residual (split-BF16 residuals, BF16 corrections), FP64 contexts run in FP64.
+ *   omega[nfreq]: host frequencies (Ha); off resonance (a frequency at a root is singular).
+ *   tol: relative residual |F - K x| / |F| to reach; max_iter: MINRES iterations per frequency.
+ *   alpha: host [nfreq][3][3]; resid (may be NULL): host [nfreq], the final relative residual
+ *   (largest of the three systems, accurate operator); iterations (may be NULL): host [nfreq].
+ * Needs dipole integrals (mu at pp_create), else PP_EINVAL.  PP_ENOTCONV if a frequency
+ * ends above 10 tol (its best estimate is written).
+ */
+pp_status pp_polarizability(pp_ctx *ctx, int nfreq, const double *omega, double tol, int max_iter, double *alpha,
+                            double *resid, int *iterations);
+
+/*
+ * Absorption spectrum of the roots in [w_lo, w_hi] (Sec. 3 spectra; Eq. pp_adc): the range is
+ * cut into nwin equal windows solved together (Sec. 2.5, the context's options; select is
+ * taken as 0 for this call), each for its kmax lowest roots; a window that returns kmax roots
+ * is halved and its halves solved again (up to 8 times), and a root found by two windows on
+ * their shared edge (within 2 res_tol) is kept once.  Then
+ *     spec[g] = sum_n f_n (eta / pi) / ((grid[g] - omega_n)^2 + eta^2)
+ * for the ngrid host frequencies in grid (Lorentzian of half width eta > 0; ngrid may be 0).
+ *   omega, osc, resid: host outputs of capacity cap (ascending omega); *nroots receives the
+ *   number of roots in the range -- if it exceeds cap nothing is written and PP_EINVAL is
+ *   returned.  PP_ENOTCONV if a window reached max_iter (its best estimates are included).
+ */
+pp_status pp_spectrum(pp_ctx *ctx, double w_lo, double w_hi, int nwin, int kmax, double eta, int ngrid,
+                      const double *grid, double *spec, int cap, double *omega, double *osc, double *resid,
+                      int *nroots);
+
+/*
  * The same batched solve driven one block iteration at a time (for callers that interleave
  * other work, and for timing single iterations).  pp_windows_begin places the windows in the
  * context's window slots (arguments as pp_solve_windows; an earlier batch that was not
@@ -210,7 +248,8 @@ pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vec
  * counters and records CUDA events around every later launch on the context's
  * stream; pp_profile(ctx, 0) stops recording.  pp_profile_read returns, for
  * kernel id 0 (the amplitude contraction GEMM, Eq. (b(2)) ladder and ring
- * parts) or id 1 (the amplitude slab generator, MP2 t of Sec. 2.2), the number
+ * parts), id 1 (the amplitude slab generator, MP2 t of Sec. 2.2) or id 2 (the
+ * launches of id 0 that ran in the split form, three BF16 products each), the number
  * of launches, their summed device milliseconds and their algorithmic FLOPs: each
  * contraction counted once, 2 M N K with K excluding the zero padding; the three BF16
  * products of the split (refinement) form count as one, and the generator counts one

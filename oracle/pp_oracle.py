@@ -27,6 +27,8 @@ is ambiguous (all pinned by the Fock-space brute force in ``fock.py``):
 * The property vector F of Eq. (pp_adc) is taken at zeroth order:
   transition moment sum_ia mu_ia (X + Y)_ia, eigenvectors normalised to
   X^T S X - Y^T S Y = 1, f = (2/3) omega |moment|^2.
+* The absorption spectrum of a frequency range is the Lorentzian-broadened sum of
+  the oscillator strengths of the roots inside the range (``range_spectrum``).
 """
 
 from __future__ import annotations
@@ -413,3 +415,51 @@ def folded_alpha(rho_k: float, a1: float, a2: float, b1: float, b2: float):
     if best_rho >= rho_k:
         return 1.0, rho(1.0)
     return best, best_rho
+
+
+# ----------------------------------------------------------------------------
+# absorption spectrum of the roots in a frequency range
+# ----------------------------------------------------------------------------
+
+
+def lorentzian(x, eta: float):
+    """Unit-area Lorentzian of half width eta: (eta / pi) / (x^2 + eta^2)."""
+    return (eta / np.pi) / (np.asarray(x) ** 2 + eta * eta)
+
+
+def range_spectrum(omega, f, w_lo: float, w_hi: float, eta: float, grid):
+    """Absorption-like spectrum of the roots inside [w_lo, w_hi] (Sec. 3): the oscillator
+    strengths broadened by a Lorentzian of half width eta,
+        S(w) = sum_{n : w_lo <= omega_n <= w_hi} f_n (eta / pi) / ((w - omega_n)^2 + eta^2),
+    i.e. -Im of the pole sum of Eq. (pp_adc) at w + i eta divided by pi, restricted to the poles
+    in the range (the frequency windows of Sec. 2.5 supply exactly those)."""
+    omega = np.asarray(omega)
+    f = np.asarray(f)
+    sel = (omega >= w_lo) & (omega <= w_hi)
+    grid = np.asarray(grid, dtype=np.float64)
+    out = np.zeros_like(grid)
+    for w_n, f_n in zip(omega[sel], f[sel]):
+        out += f_n * lorentzian(grid - w_n, eta)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# frequency-dependent linear response
+# ----------------------------------------------------------------------------
+
+
+def polarizability(M: np.ndarray, Sig: np.ndarray, mu: np.ndarray, omega: float) -> np.ndarray:
+    """Dipole polarizability at a real frequency, Eq. (pp_adc) with F_c = (mu_c; mu_c):
+    alpha[c, c'] = F_c^T (M - omega Sigma)^-1 F_c', by a dense linear solve."""
+    m = mu.reshape(3, -1)
+    F = np.concatenate([m, m], axis=1).T  # [2 ov, 3]
+    X = np.linalg.solve(M - omega * Sig, F)
+    return F.T @ X
+
+
+def polarizability_sum_over_states(omega_n, X, Y, mu, omega: float) -> np.ndarray:
+    """The same tensor from the roots: sum_n 2 omega_n (mu_c . u_n)(mu_c' . u_n) / (omega_n^2 - omega^2),
+    u_n = X_n + Y_n (eigenvectors normalised to X^T S X - Y^T S Y = 1)."""
+    mom = mu.reshape(3, -1) @ (X + Y)  # [3, n]
+    wts = 2.0 * omega_n / (omega_n ** 2 - omega ** 2)
+    return (mom * wts[None, :]) @ mom.T

@@ -28,7 +28,7 @@ STATUS_NAMES = {
 # every symbol declared in include/pp.h
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
-    "pp_solve_windows", "pp_windows_begin", "pp_windows_step", "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
+    "pp_solve_windows", "pp_polarizability", "pp_spectrum", "pp_windows_begin", "pp_windows_step", "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
     "pp_last_error", "pp_server_create", "pp_server_add_dot", "pp_server_submit", "pp_server_wait",
     "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
 )
@@ -39,7 +39,7 @@ class pp_options(C.Structure):
         ("prec", C.c_int), ("order", C.c_int), ("block", C.c_int), ("m_max", C.c_int),
         ("max_iter", C.c_int), ("res_tol", C.c_double), ("jacobi_floor", C.c_double),
         ("select", C.c_int), ("refine", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
-        ("workspace_gb", C.c_double),
+        ("workspace_gb", C.c_double), ("tda", C.c_int),
     ]
 
 
@@ -91,6 +91,11 @@ def load(path: str | None = None):
         lib.pp_solve_windows.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int), _dp, _dp, _dp,
                                          C.POINTER(C.c_int)]
         lib.pp_solve_windows.restype = C.c_int
+        lib.pp_polarizability.argtypes = [vp, C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
+        lib.pp_polarizability.restype = C.c_int
+        lib.pp_spectrum.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp,
+                                    C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int)]
+        lib.pp_spectrum.restype = C.c_int
         lib.pp_windows_begin.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
         lib.pp_windows_begin.restype = C.c_int
         lib.pp_windows_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
@@ -289,6 +294,40 @@ def pp_solve_windows(ctx, omega0, delta, k, allow_notconv: bool = False):
     return out, st
 
 
+def pp_polarizability(ctx, omega, tol: float = 1e-8, max_iter: int = 2000, allow_notconv: bool = False):
+    """Dipole polarizability alpha[f][c][c'] at real frequencies: dict(alpha, resid, iterations, status)."""
+    lib = load()
+    w = _f64(omega).ravel()
+    alpha = np.zeros((w.size, 3, 3))
+    res = np.zeros(w.size)
+    its = np.zeros(w.size, dtype=np.int32)
+    st = lib.pp_polarizability(ctx, int(w.size), _ptr(w), float(tol), int(max_iter), _ptr(alpha), _ptr(res),
+                               its.ctypes.data_as(C.POINTER(C.c_int)))
+    if not (allow_notconv and st == PP_ENOTCONV):
+        _check(st, ctx)
+    return dict(alpha=alpha, resid=res, iterations=its, status=st)
+
+
+def pp_spectrum(ctx, w_lo: float, w_hi: float, nwin: int, kmax: int, eta: float, grid, cap: int = 4096,
+                allow_notconv: bool = False):
+    """Roots and Lorentzian-broadened absorption spectrum of [w_lo, w_hi]: dict(spec, omega, osc,
+    resid, status)."""
+    lib = load()
+    g = _f64(grid).ravel()
+    spec = np.zeros_like(g)
+    om = np.zeros(cap)
+    osc = np.zeros(cap)
+    res = np.zeros(cap)
+    n = C.c_int(0)
+    st = lib.pp_spectrum(ctx, float(w_lo), float(w_hi), int(nwin), int(kmax), float(eta), int(g.size),
+                         _ptr(g) if g.size else None, _ptr(spec) if g.size else None, int(cap), _ptr(om), _ptr(osc),
+                         _ptr(res), C.byref(n))
+    if not (allow_notconv and st == PP_ENOTCONV):
+        _check(st, ctx)
+    k = n.value
+    return dict(spec=spec, omega=om[:k], osc=osc[:k], resid=res[:k], status=st)
+
+
 class WindowRun:
     """pp_windows_begin / pp_windows_step / pp_windows_end: a batched window solve driven one
     block iteration at a time."""
@@ -388,6 +427,12 @@ class Dot:
 
     def windows(self, omega0, delta, k):
         return WindowRun(self.ctx, omega0, delta, k)
+
+    def polarizability(self, omega, **kw):
+        return pp_polarizability(self.ctx, omega, **kw)
+
+    def spectrum(self, w_lo, w_hi, nwin, kmax, eta, grid, **kw):
+        return pp_spectrum(self.ctx, w_lo, w_hi, nwin, kmax, eta, grid, **kw)
 
     def stats(self):
         return pp_last_stats(self.ctx)

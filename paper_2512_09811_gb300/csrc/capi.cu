@@ -96,7 +96,7 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
   else pp_default_options(&o);
   if (o.order < 0 || o.order > 2 || (o.prec != PP_FP64 && o.prec != PP_BF16 && o.prec != PP_BF16X3) || o.block < 1 ||
       o.m_max < 4 || !(o.res_tol > 0) || !(o.jacobi_floor > 0) || (o.select != 0 && o.select != 1) ||
-      !(o.workspace_gb >= 0) || o.workspace_gb > 1e5) {
+      !(o.workspace_gb >= 0) || o.workspace_gb > 1e5 || (o.tda != 0 && o.tda != 1)) {
     g_create_err = "pp_create: bad options";
     return PP_EINVAL;
   }
@@ -268,6 +268,36 @@ extern "C" pp_status pp_solve_windows(pp_ctx *c, int nwin, const double *omega0,
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     return st;
+  });
+}
+
+extern "C" pp_status pp_polarizability(pp_ctx *c, int nfreq, const double *omega, double tol, int max_iter,
+                                       double *alpha, double *resid, int *iterations) {
+  if (!c) return PP_EINVAL;
+  if (nfreq < 1 || !omega || !alpha || !(tol > 0) || max_iter < 1 || !all_finite(omega, (size_t)nfreq)) {
+    c->err = "pp_polarizability: bad argument";
+    return PP_EINVAL;
+  }
+  return guarded(c, [&]() -> pp_status {
+    return polarizability_impl(c, nfreq, omega, tol, max_iter, alpha, resid, iterations);
+  });
+}
+
+extern "C" pp_status pp_spectrum(pp_ctx *c, double w_lo, double w_hi, int nwin, int kmax, double eta, int ngrid,
+                                 const double *grid, double *spec, int cap, double *omega, double *osc,
+                                 double *resid, int *nroots) {
+  if (!c) return PP_EINVAL;
+  if (!std::isfinite(w_lo) || !std::isfinite(w_hi) || !(w_hi > w_lo) || nwin < 1 || kmax < 1 || !(eta > 0) ||
+      ngrid < 0 || (ngrid > 0 && (!grid || !spec)) || cap < 0 || !nroots || (cap > 0 && (!omega || !osc || !resid))) {
+    c->err = "pp_spectrum: bad argument";
+    return PP_EINVAL;
+  }
+  if (ngrid > 0 && !all_finite(grid, (size_t)ngrid)) {
+    c->err = "pp_spectrum: non-finite grid point";
+    return PP_EINVAL;
+  }
+  return guarded(c, [&]() -> pp_status {
+    return spectrum_impl(c, w_lo, w_hi, nwin, kmax, eta, ngrid, grid, spec, cap, omega, osc, resid, nroots);
   });
 }
 

@@ -196,5 +196,12 @@ pp_status windows_begin(pp_ctx *c, int nwin, const double *omega0, const double 
 pp_status windows_step(pp_ctx *c, int *unfinished, long long *sigma_vectors, int *sigma_calls);
 pp_status windows_end(pp_ctx *c, double *omega, double *osc, double *resid, int *nfound);
 void window_run_destroy(pp_ctx *c);
+// absorption spectrum of a frequency range from stitched window solves (spectrum.cu)
+pp_status spectrum_impl(pp_ctx *c, double w_lo, double w_hi, int nwin, int kmax, double eta, int ngrid,
+                        const double *grid, double *spec, int cap, double *omega, double *osc, double *resid,
+                        int *nroots);
+// frequency-dependent dipole polarizability by preconditioned MINRES (response.cu)
+pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double tol, int max_iter, double *alpha,
+                              double *resid, int *iterations);
 // dispatch of one sigma application (solver and C ABI)
 void apply_sigma(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, int prec);

@@ -12,7 +12,8 @@
 //   P_Q      = T C_Q(V),  C_Q(V) = V Bvv_Q - Boo_Q V,  T[(i,c),(j,d)] = t_ij^cd.
 // The last form gathers the particle and hole ladders and the (ki|bc)/(kj|ac)
 // ring parts of Eq. (b(2)) into one contraction with the amplitudes; Gam carries
-// the (kc|bi)/(kc|aj) ring parts.  sigma_X = A X + B Y, sigma_Y = B X + A Y.
+// the (kc|bi)/(kc|aj) ring parts.  sigma_X = A X + B Y, sigma_Y = B X + A Y; in the
+// Tamm-Dancoff form (B = 0) sigma_X = A X, sigma_Y = A Y and no B term is formed.
 #pragma once
 #include <functional>
 
@@ -99,7 +100,8 @@ __global__ void k_metric(double *__restrict__ met, const double *__restrict__ V,
   }
 }
 // sigma[s][0] = Aacc[2s] + Bacc[2s+1];  sigma[s][1] = Bacc[2s] + Aacc[2s+1]
-// (gap64 set: the diagonal term gap * V is added here in FP64 instead of living in Aacc)
+// (gap64 set: the diagonal term gap * V is added here in FP64 instead of living in Aacc;
+// Bacc null: the Tamm-Dancoff form, sigma = (A X, A Y))
 template <class T>
 __global__ void k_combine(double *__restrict__ sig, const T *__restrict__ Aacc,
                           const T *__restrict__ Bacc, const double *__restrict__ gap64,
@@ -107,7 +109,7 @@ __global__ void k_combine(double *__restrict__ sig, const T *__restrict__ Aacc,
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
     long long r = p / ov, e = p % ov;
-    double x = (double)Aacc[p] + (double)Bacc[(r ^ 1) * ov + e];
+    double x = (double)Aacc[p] + (Bacc ? (double)Bacc[(r ^ 1) * ov + e] : 0.0);
     if (gap64) x += gap64[e] * V64[p];
     sig[p] = x;
   }
@@ -126,6 +128,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
                  const SigmaRes<T> &res, const SigmaWork<T> &wk, const SigmaHooks<T> &hk) {
   using namespace sigma_detail;
   const int o = c->o, v = c->v, Q = c->Q, order = c->opt.order;
+  const bool tda = c->opt.tda != 0;  // Tamm-Dancoff form: no B terms
   const long long ov = c->ov;
   cudaStream_t s = c->stream;
   T *Aacc = wk.Aacc, *Bacc = wk.Bacc;
@@ -162,7 +165,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     k_add<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, Bacc, tot);
     PP_LAUNCH_CHECK("k_add");
     if (hk.first_order && hk.first_order(R, Aacc, Bacc)) {
-      if (order >= 2) hk.amplitude(R, nullptr, Bacc);
+      if (order >= 2 && !tda) hk.amplitude(R, nullptr, Bacc);
     } else {
       T *W = wk.W;  // W[r][j][Q][d] = V_r BvvP
       const long long oQv = (long long)o * Q * v;
@@ -181,6 +184,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
       ka.C = Aacc; ka.c_m = v; ka.c_n = 1; ka.c_batch = ov; ka.alpha = T(-1); ka.beta = T(1);
       if (split_k<T>()) ka.ksplit = 16;
       gemm<T>(ka, s);
+      if (!tda) {
       T *EF = wk.EF;  // E[r][Q][i][j] = sum_b Bov[Q][i][b] V[r][j][b]; F likewise with Gam
       const long long efb = 2LL * Q * o * o;
       if (!(hk.ef && hk.ef(R, V, EF, order >= 2))) {
@@ -223,6 +227,7 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
         PP_LAUNCH_CHECK("k_cmat");
         hk.amplitude(R, (const T *)U, Bacc);
       }
+      }  // !tda
     }
   }
   if (order >= 2) {
@@ -245,7 +250,8 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     k_a2<T><<<ew_grid(tot), 256, 0, s>>>(Aacc, t1, t2, t3, t4, res.eps, o, v, tot);
     PP_LAUNCH_CHECK("k_a2");
   }
-  k_combine<T><<<ew_grid(tot), 256, 0, s>>>(sig, Aacc, Bacc, diag64 ? c->gap.as<double>() : nullptr, V64, ov, tot);
+  k_combine<T><<<ew_grid(tot), 256, 0, s>>>(sig, Aacc, tda ? nullptr : Bacc, diag64 ? c->gap.as<double>() : nullptr,
+                                            V64, ov, tot);
   PP_LAUNCH_CHECK("k_combine");
   if (met) {
     k_metric<T><<<ew_grid(tot), 256, 0, s>>>(met, V64, t1, t3, order >= 2, ov, tot);

@@ -1692,10 +1692,23 @@ struct WindowBatch {
       finalize(wi, PP_ENOTCONV);
       return 0;
     }
+    // columns that get a direction: every unconverged block column, except in the split
+    // (refinement) phase, where the products cost three times as much and the roots the
+    // window needs (with their guards) are already close: only those, unless all of them
+    // have converged and the window still has to move or widen
+    std::vector<int> sel;
+    const bool refining = refine && wi.prec == PP_BF16X3;
+    if (refining) {
+      for (int j : need)
+        if (!(wi.h_res[j] <= wi.tol)) sel.push_back(j);
+      std::sort(sel.begin(), sel.end());
+    }
+    if (sel.empty())
+      for (int j = 0; j < b; ++j)
+        if (!(wi.h_res[j] <= wi.tol)) sel.push_back(j);
     wi.active.clear();
     int nd = 0;
-    for (int j = 0; j < b; ++j) {
-      if (wi.h_res[j] <= wi.tol) continue;
+    for (int j : sel) {  // ascending, so a column moves only towards the front
       if (nd != j)
         PP_CUDA(cudaMemcpyAsync(Dcols + (long long)nd * L, Dcols + (long long)j * L, vecbytes,
                                 cudaMemcpyDeviceToDevice, s));
@@ -1710,15 +1723,16 @@ struct WindowBatch {
     return nd;
   }
 
-  // refinement: restart the window on its folded targets and the next Rayleigh-Ritz vectors,
-  // recompute their products with the split (FP32-level) tensor-core sigma
+  // refinement: restart the window on its folded target vectors and recompute their
+  // products with the split (FP32-level) tensor-core sigma
   void switch_to_split(Window &wi) {
     const int m = wi.m, b = wi.bx;
     const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));
     PP_CUDA(cudaMemcpyAsync(wi.Kc, wi.Cref, sizeof(double) * b * m, cudaMemcpyDeviceToDevice, s));
     PP_CUDA(cudaMemcpyAsync(wi.Kc + (long long)b * m, wi.Esel, sizeof(double) * nsel * m,
                             cudaMemcpyDeviceToDevice, s));
-    const int nout = std::min(64, std::min(m, 2 * b));
+    // the folded vectors of the block only: each kept vector costs a split-form product
+    const int nout = std::min(64, std::min(m, b));
     k_mgs<<<1, RT, 0, s>>>(wi.Kc, m, b + nsel, nout, wi.Qk, wi.dkept, 1e-20);
     PP_LAUNCH_CHECK("k_mgs");
     int kept = 0;

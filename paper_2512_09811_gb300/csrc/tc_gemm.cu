@@ -1055,12 +1055,15 @@ void tgen_p(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long l
 // plan: BF16 / FP32 resident copies and workspaces of the tensor-core form
 // ---------------------------------------------------------------------------
 // per-kernel launch timing of the tensor-core form (enabled by pp_profile)
+// ids: 0 the amplitude-contraction GEMM (all launches), 1 the amplitude generator, 2 the
+// amplitude-contraction GEMM launches of the split form (three BF16 products each)
+constexpr int NPROF = 3;
 struct KernelProfile {
   bool on = false;
-  std::vector<cudaEvent_t> ev[2];  // start/stop pairs per kernel id
-  long long launches[2] = {0, 0};
-  double flops[2] = {0, 0};
-  double ms[2] = {0, 0};
+  std::vector<cudaEvent_t> ev[NPROF];  // start/stop pairs per kernel id
+  long long launches[NPROF] = {0, 0, 0};
+  double flops[NPROF] = {0, 0, 0};
+  double ms[NPROF] = {0, 0, 0};
 };
 struct TcPlan {
   long long ldq = 0, ldT = 0, vp = 0, Qp = 0;
@@ -1137,7 +1140,7 @@ static void prof_mark(KernelProfile &pr, int id, cudaStream_t s) {
 }
 // fold recorded event pairs into the totals (synchronises on the last event)
 static void prof_collect(KernelProfile &pr) {
-  for (int id = 0; id < 2; ++id) {
+  for (int id = 0; id < NPROF; ++id) {
     auto &v = pr.ev[id];
     for (size_t k = 0; k + 1 < v.size(); k += 2) {
       PP_CUDA(cudaEventSynchronize(v[k + 1]));
@@ -1470,6 +1473,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     hk.first_order = [&](int Rc, float *Aacc, float *Bacc) {
       const int nseg1 = 3;
       const int order = c->opt.order;
+      const bool tda = c->opt.tda != 0;  // Tamm-Dancoff form: only U and KA (A terms)
       const long long kbo = p->kbo, kqv = p->kqv, kef = p->kef;
       bf *kuh = p->kaU_hi.as<bf>(), *kul = p->kaU_lo.as<bf>();
       bf *efh = p->efB_hi.as<bf>(), *efl = p->efB_lo.as<bf>();
@@ -1496,7 +1500,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d), written as
       // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction; U[r][Q][j][d]
       // is element (r o + j, Q v + d) of the pair above, i.e. row * kqv + column
-      if (order >= 2) {
+      if (order >= 2 && !tda) {
         seg3(vhi, vlo, p->bvv_hi.as<bf>(), p->bvv_lo.as<bf>(), A, B);
         tc::GemmOut cc;
         cc.Chi = p->c_hi.as<bf>();
@@ -1525,6 +1529,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.accumulate = 1;
         tc::gemm_bf16(Rc * o, v, kqv, nseg1, A, kqv, B, kqv, out, err, s);
       }
+      if (tda) return true;
       // E and F: EF[(r,i)][(t,j)] = sum_b X_t[i][b] V[r][j][b], X = Bov (t < Q), Gamma (t >= Q)
       {
         tc::GemmOut out;
@@ -1602,11 +1607,17 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         o2.d_c = Q;
         o2.s_c1 = ov * Qp;
         prof_mark(p->prof, 0, s);
+        if (split) prof_mark(p->prof, 2, s);
         tc::gemm_bf16((int)rows, (int)NC, ldT, nseg, A, ldT, B, ldT, o1, err, s, &o2);
         prof_mark(p->prof, 0, s);
+        if (split) prof_mark(p->prof, 2, s);
         if (p->prof.on) {  // algorithmic: the contraction once (the split form's three
           p->prof.launches[0] += 1;  // products are an emulation of one)
           p->prof.flops[0] += 2.0 * (double)rows * (double)NC * (double)ov;
+          if (split) {
+            p->prof.launches[2] += 1;
+            p->prof.flops[2] += 2.0 * (double)rows * (double)NC * (double)ov;
+          }
         }
       }
       // Bacc[(r,i)][a] += sum_(c,q) P1[(r,i)][(c,q)] Bvv[q][c][a]
@@ -1657,7 +1668,7 @@ extern "C" pp_status pp_profile(pp_ctx *c, int enable) {
     prof_collect(p->prof);
     p->prof.on = enable != 0;
     if (enable)
-      for (int id = 0; id < 2; ++id) {
+      for (int id = 0; id < NPROF; ++id) {
         p->prof.launches[id] = 0;
         p->prof.flops[id] = 0;
         p->prof.ms[id] = 0;
@@ -1670,7 +1681,7 @@ extern "C" pp_status pp_profile(pp_ctx *c, int enable) {
 }
 
 extern "C" pp_status pp_profile_read(pp_ctx *c, int id, long long *launches, double *ms, double *flops) {
-  if (!c || id < 0 || id > 1) return PP_EINVAL;
+  if (!c || id < 0 || id >= NPROF) return PP_EINVAL;
   try {
     TcPlan *p = tc_plan(c);
     prof_collect(p->prof);

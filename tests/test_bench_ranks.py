@@ -34,3 +34,19 @@ def test_two_rank_reduction():
     for rank, ms, roots, w in out:
         assert ms == 150.0 and roots == 15.0
     assert out[0][3] == pytest.approx(1.0) and out[1][3] == pytest.approx(1.1)
+
+
+def test_rank_windows_are_disjoint_and_flop_model():
+    import bench
+
+    ranks = [bench.windows_for_rank(1.0, 0.05, 8, r) for r in range(4)]
+    starts = sorted(x for r in ranks for x in r)
+    assert len(starts) == 32 and all(b - a == pytest.approx(0.05) for a, b in zip(starts, starts[1:]))
+    assert ranks[1][0] == pytest.approx(1.0 + 8 * 0.05)
+    # the amplitude contraction 2 (ov)^2 Q per half-vector dominates the per-vector work
+    o, v, Q = 128, 512, 1536
+    per_vec = bench.sigma_flops_per_vector(o, v, Q)
+    ladder = 2 * 2.0 * (o * v) ** 2 * Q
+    assert ladder < per_vec < 1.05 * ladder
+    assert bench.tgen_flops(o, v, Q) == 2.0 * Q * (o * v) ** 2
+    assert bench.step_flops(o, v, Q, 10, 2) == 10 * per_vec + 2 * bench.tgen_flops(o, v, Q)

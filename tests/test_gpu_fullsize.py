@@ -1,22 +1,33 @@
-"""Parity at the benchmark's full size (nocc 64, nvir 256, naux 768; ph dimension 16384).
+"""Parity at the full sizes of the benchmark dots.
 
-The dense oracle is out of reach here (M has 32768^2 entries and the particle ladder
-needs 256^4 integrals), so parity is checked on what the oracle can compute:
-its matrix-free FP64 sigma for sampled trial vectors, and the FP64 residual
-|M x - theta Sigma x| of the roots the solver returns (for a symmetric-definite-
-like pencil the eigenvalue error is bounded by the residual over the gap, and
-theta is the oracle's own Rayleigh quotient of x).
+64/256/768 (ph dimension 16384): the dense oracle is out of reach (M has 32768^2 entries and
+the particle ladder needs 256^4 integrals), so parity is checked on what the oracle can
+compute -- its matrix-free FP64 sigma of sampled trial vectors, element by element (FP64 to
+1e-12 relative; BF16 and split forms within the per-element bounds of test_gpu_bf16.py) --
+and on the window the bench solves: every returned root is an eigenpair of the FP64
+operator to the solver tolerance.  The GPU FP64 sigma, pinned to the oracle to 1e-12 in
+this file, checks all 8 roots; the oracle itself checks the lowest and highest.  For a
+root isolated by a gap delta from the other roots the Rayleigh quotient theta is within
+|r|^2 / delta of the root; the test asserts that this estimate is below 1e-6 Ha, and that
+the reported root is within 5e-7 Ha of the FP64 Rayleigh quotient.
+
+128/512/1536 (ph dimension 65536): the oracle's amplitude array alone would take 34 GB, so
+the FP64 GPU sigma is checked through a property that holds at any size (M and Sigma
+symmetric) and then used to check three of the roots of a mixed-form window (an FP64
+sigma takes ~20 s per supervector at this size).
 """
 
 import numpy as np
 import pytest
 
 from oracle import pp_oracle as po
+from sigma_bounds import sigma_scales
 from synth.inputs import make_inputs, random_vectors
 
 pytestmark = pytest.mark.gpu
 
 O, V, Q = 64, 256, 768
+BOUNDS = {"PP_BF16": (8.0, 2.0 ** -8, 1e-6), "PP_BF16X3": (16.0, 2.0 ** -16, 2e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -29,28 +40,34 @@ def oracle_sigma(dot_inputs):
     return po.SigmaRef(dot_inputs.eps, dot_inputs.B, O, order=2)
 
 
-def test_fullsize_sigma_fp64_and_bf16(cuda_lib, dot_inputs, oracle_sigma):
+def test_fullsize_sigma_elementwise(cuda_lib, dot_inputs, oracle_sigma):
     pp = cuda_lib
     Z = random_vectors(1, O, V, seed=21)
     want = oracle_sigma.sigma(Z)
-    want1 = po.SigmaRef(dot_inputs.eps, dot_inputs.B, O, order=1).sigma(Z)
-    second = np.linalg.norm(want - want1)
+    scale = sigma_scales(oracle_sigma, Z)
+    smax = np.abs(want).max()
     dot = pp.Dot(dot_inputs, order=2)
     try:
         got = dot.sigma(Z)
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
-        got_bf = dot.sigma(Z, prec=pp.PP_BF16)
-        assert np.linalg.norm(got_bf - want) <= 2.0 ** -8 * 4 * second + 1e-5 * np.linalg.norm(want)
-        got_x3 = dot.sigma(Z, prec=pp.PP_BF16X3)
-        assert np.linalg.norm(got_x3 - want) <= 1e-6 * np.linalg.norm(want)
+        assert np.abs(got - want).max() <= 1e-12 * smax
+        for name in ("PP_BF16", "PP_BF16X3"):
+            kappa, u, floor = BOUNDS[name]
+            g = dot.sigma(Z, prec=getattr(pp, name))
+            ratio = np.abs(g - want) / (kappa * u * scale + floor * smax)
+            assert ratio.max() <= 1.0, (name, float(ratio.max()))
     finally:
         dot.close()
 
 
-def test_fullsize_window_roots_have_small_oracle_residual(cuda_lib, dot_inputs, oracle_sigma):
-    """The bench's solve (BF16 sigma, FP64 Krylov, split-BF16 refinement to a residual of 1e-6):
-    each returned root is an eigenpair to a few 1e-6 in the oracle's FP64 arithmetic, so the
-    root lies within that distance of theta (and within |r|^2 / gap of it when isolated)."""
+def _rq_and_residual(Mz, Sz, z):
+    norm = z @ Sz
+    theta = (z @ Mz) / norm
+    return theta, np.linalg.norm(Mz - theta * Sz) / abs(norm), norm
+
+
+def test_fullsize_window_all_roots(cuda_lib, dot_inputs, oracle_sigma):
+    """The bench's solve (BF16 sigma, FP64 Krylov, split-BF16 refinement to 1e-6)."""
     pp = cuda_lib
     dot = pp.Dot(dot_inputs, prec=pp.PP_BF16, order=2, select=0, res_tol=1e-6, max_iter=300)
     try:
@@ -59,17 +76,73 @@ def test_fullsize_window_roots_have_small_oracle_residual(cuda_lib, dot_inputs, 
         out = dot.solve_window(w0, 0.1, 8, want_vectors=True)
     finally:
         dot.close()
-    assert len(out["omega"]) == 8
-    assert np.all(np.diff(out["omega"]) > 0)
-    assert np.all(out["omega"] >= w0) and np.all(out["omega"] <= w0 + 0.1)
-    for n in (0, 7):
-        z = out["vectors"][n][None]
-        Mz = oracle_sigma.sigma(z)[0].ravel()
-        Sz = oracle_sigma.metric(z)[0].ravel()
-        zz = z[0].ravel()
-        norm = zz @ Sz
+    om = out["omega"]
+    assert len(om) == 8
+    assert np.all(np.diff(om) > 0)
+    assert np.all(om >= w0) and np.all(om <= w0 + 0.1)
+    Z = out["vectors"]
+    # all 8 with the FP64 GPU sigma (pinned to the oracle above and here)
+    f64 = pp.Dot(dot_inputs, prec=pp.PP_FP64, order=2)
+    try:
+        MZ, SZ = f64.sigma(Z, metric=True)
+    finally:
+        f64.close()
+    gaps = np.array([np.min(np.abs(np.delete(om, n) - om[n])) for n in range(8)])
+    for n in range(8):
+        z = Z[n].ravel()
+        theta, r, norm = _rq_and_residual(MZ[n].ravel(), SZ[n].ravel(), z)
         assert abs(norm - 1.0) < 1e-5  # X^T S X - Y^T S Y = 1
-        theta = (zz @ Mz) / norm
-        assert abs(theta - out["omega"][n]) < 1e-6
-        r = Mz - theta * Sz
-        assert np.linalg.norm(r) / abs(norm) < 5e-6
+        assert abs(theta - om[n]) < 5e-7  # reported root vs the FP64 Rayleigh quotient
+        assert r <= 1.2e-6  # solver tolerance plus the split form's operator error
+        if gaps[n] > 1e-5:  # isolated from the other roots found
+            assert r * r / gaps[n] <= 1e-6, (n, r, gaps[n])
+    # the lowest and the highest with the oracle itself
+    for n in (0, 7):
+        z = Z[n][None]
+        Mz = oracle_sigma.sigma(z)[0].ravel()
+        np.testing.assert_allclose(Mz, MZ[n].ravel(), rtol=0, atol=1e-12 * np.abs(Mz).max())
+        theta, r, _ = _rq_and_residual(Mz, oracle_sigma.metric(z)[0].ravel(), Z[n].ravel())
+        assert abs(theta - om[n]) < 5e-7 and r <= 1.2e-6
+
+
+def test_c3_fp64_sigma_properties_and_roots(cuda_lib):
+    """128/512/1536: FP64 GPU sigma symmetric; mixed-form window roots are eigenpairs of it
+    to the solver tolerance."""
+    import torch
+
+    pp = cuda_lib
+    o, v, Q = 128, 512, 1536
+    inp = make_inputs(o, v, Q, seed=2, mode="perturbative", b_dtype=np.float32)
+    f64 = pp.Dot(inp, prec=pp.PP_FP64, order=2)
+    mixed = pp.Dot(inp, prec=pp.PP_BF16, order=2, select=0, res_tol=1e-6, block=16, max_iter=300)
+    try:
+        Zh = random_vectors(2, o, v, seed=31)
+        Z = torch.from_numpy(Zh).cuda()
+        MZ, SZ = pp.pp_sigma(f64.ctx, Z, pp.PP_FP64, metric=True)
+        MZ, SZ = MZ.cpu().numpy().reshape(2, -1), SZ.cpu().numpy().reshape(2, -1)
+        z = Zh.reshape(2, -1)
+        scale = np.linalg.norm(MZ[0]) * np.linalg.norm(z[1])
+        assert abs(z[1] @ MZ[0] - z[0] @ MZ[1]) <= 1e-12 * scale  # M symmetric
+        assert abs(z[1] @ SZ[0] - z[0] @ SZ[1]) <= 1e-12 * np.linalg.norm(SZ[0]) * np.linalg.norm(z[1])
+        dA, dS = mixed.diagonal()
+        w0 = float(np.percentile((dA / dS).ravel(), 20))
+        out = mixed.solve_window(w0, 0.05, 8, want_vectors=True)
+        om = out["omega"]
+        assert len(om) == 8 and np.all(out["resid"] <= 1e-6)
+        pick = [0, 4, 7]
+        Zr = torch.from_numpy(np.ascontiguousarray(out["vectors"][pick])).cuda()
+        Mr, Sr = pp.pp_sigma(f64.ctx, Zr, pp.PP_FP64, metric=True)
+        Mr, Sr = Mr.cpu().numpy(), Sr.cpu().numpy()
+        for t, n in enumerate(pick):
+            theta, r, norm = _rq_and_residual(Mr[t].ravel(), Sr[t].ravel(), out["vectors"][n].ravel())
+            assert abs(norm - 1.0) < 1e-5
+            assert abs(theta - om[n]) < 5e-7
+            # the solver converges the split form's residual to 1e-6; the split operator's own
+            # error grows with the reductions (K = ov = 65536 here) and adds up to ~5e-7
+            assert r <= 2e-6
+            gap = np.min(np.abs(np.delete(om, n) - om[n]))
+            if gap > 1e-5:
+                assert r * r / gap <= 1e-6
+    finally:
+        f64.close()
+        mixed.close()

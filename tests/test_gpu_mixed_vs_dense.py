@@ -117,3 +117,28 @@ def test_stepped_windows_match_dense(cuda_lib, case):
     for (w0, width, k), got in zip(wins, outs):
         assert np.all(got["resid"] <= 1e-6)
         _check(got, ref, w0, width, k, 1e-6, mixed=True)
+
+
+@pytest.mark.parametrize("prec_name,tol", [("PP_FP64", 1e-8), ("PP_BF16", 1e-6)])
+def test_range_spectrum_matches_dense(cuda_lib, case, prec_name, tol):
+    """Absorption spectrum of a 0.02 Ha range (Sec. 3) from stitched windows against the
+    dense oracle's roots and strengths: every root in the range found once (windows of 0.004
+    Ha, at most 6 roots each before a window is halved), and the broadened spectrum within
+    1e-4 (FP64 form) or 2e-3 (mixed form) of its maximum."""
+    pp = cuda_lib
+    inp, ref, wins = case
+    w_lo = wins[0][0]
+    w_hi = w_lo + 0.02
+    eta = 1e-3
+    grid = np.linspace(w_lo - 0.005, w_hi + 0.005, 301)
+    dot = pp.Dot(inp, prec=getattr(pp, prec_name), order=2, select=0, res_tol=tol, max_iter=300)
+    try:
+        got = dot.spectrum(w_lo, w_hi, 5, 6, eta, grid)
+    finally:
+        dot.close()
+    want_idx = np.nonzero((ref["omega"] >= w_lo) & (ref["omega"] <= w_hi))[0]
+    assert len(got["omega"]) == len(want_idx) and len(want_idx) > 10
+    np.testing.assert_allclose(got["omega"], ref["omega"][want_idx], atol=tol, rtol=0)
+    want = po.range_spectrum(ref["omega"], ref["f"], w_lo, w_hi, eta, grid)
+    rel = np.abs(got["spec"] - want).max() / want.max()
+    assert rel <= (1e-4 if prec_name == "PP_FP64" else 2e-3), rel

@@ -242,3 +242,71 @@ def test_variance_is_paper_definition_for_unit_metric():
         rho2 = xn @ (A @ A) @ xn
         assert po.variance(A, np.eye(7), x, rho) == pytest.approx(rho2 - rho * rho, rel=1e-12)
         assert rho2 - rho * rho > 1e-3  # not an eigenvector
+
+
+def test_range_spectrum_closed_forms():
+    """Spectrum of a frequency range (Sec. 3): each root contributes a unit-area Lorentzian
+    times f_n, so over [a, b] its integral is f_n (atan((b - w_n)/eta) - atan((a - w_n)/eta))/pi
+    (trapezoid sum on a fine grid against that closed form); roots outside the range do not
+    contribute; an isolated root's peak height is f_n / (pi eta)."""
+    omega = np.array([0.9, 1.0, 1.02, 1.3])
+    f = np.array([0.7, 0.2, 0.5, 9.0])
+    eta = 0.004
+    a, b = 0.95, 1.1
+    grid = np.linspace(0.5, 1.6, 400001)
+    S = po.range_spectrum(omega, f, a, b, eta, grid)
+    want = sum(fn * (np.arctan((grid[-1] - wn) / eta) - np.arctan((grid[0] - wn) / eta)) / np.pi
+               for wn, fn in zip(omega[1:3], f[1:3]))
+    integral = float(np.sum(0.5 * (S[1:] + S[:-1]) * np.diff(grid)))
+    assert integral == pytest.approx(want, rel=1e-6)
+    peak = po.range_spectrum(omega, f, a, b, eta, [1.0])[0]
+    tail = 0.5 * (eta / np.pi) / (0.02 ** 2 + eta ** 2)
+    assert peak == pytest.approx(0.2 / (np.pi * eta) + tail, rel=1e-12)
+    assert np.all(po.range_spectrum(omega, f, 2.0, 3.0, eta, grid) == 0.0)
+
+
+def test_tamm_dancoff_first_order_is_cis():
+    """Tamm-Dancoff form (B = 0): at first order its roots are the eigenvalues of the CIS
+    Hamiltonian built from determinants (Fock-space brute force); at second order they are
+    the generalized eigenvalues of (A, S) from scipy's symmetric-definite solver."""
+    import scipy.linalg as sl
+
+    o, v = 3, 4
+    inp = make_inputs(o, v, 5, seed=5, sigma_b=0.2)
+    pe = fock.PerturbativeElements(inp.eps, inp.B, o)
+    H = pe.H0 + pe.W
+    ref = pe.ref
+    e_hf = ref @ (H @ ref)
+    Sd = np.array([pe.fs.cre[o + a] @ (pe.fs.ann[i] @ ref) for i in range(o) for a in range(v)])
+    cis = Sd @ (H @ Sd.T) - e_hf * (Sd @ Sd.T)
+    S1, A1, B1 = po.dense_blocks(inp.eps, inp.B, o, order=1)
+    tda1 = po.solve_dense(S1, A1, np.zeros_like(B1))
+    np.testing.assert_allclose(tda1["omega"], np.linalg.eigvalsh(cis), atol=1e-12)
+    np.testing.assert_allclose(tda1["Y"], 0.0, atol=1e-14)
+    S2, A2, B2 = po.dense_blocks(inp.eps, inp.B, o, order=2)
+    tda2 = po.solve_dense(S2, A2, np.zeros_like(B2))
+    np.testing.assert_allclose(tda2["omega"], sl.eigh(A2, S2, eigvals_only=True), atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_polarizability_two_routes(tiny, order):
+    """Eq. (pp_adc) at real frequencies: the dense solve of (M - omega Sigma) x = F equals the
+    sum over the roots, 2 omega_n (mu . u_n)^2 / (omega_n^2 - omega^2), below the first root and
+    between two roots; at order 0 it is the closed form sum_ia 2 D_ia mu_ia mu_ia / (D_ia^2 - omega^2)."""
+    o = tiny.nocc
+    S, A, Bm = po.dense_blocks(tiny.eps, tiny.B, o, order)
+    M, Sig = po.assemble_M(tiny.eps, tiny.B, o, order)
+    res = po.solve_dense(S, A, Bm, tiny.mu)
+    om = res["omega"]
+    for w in (0.5 * om[0], 0.5 * (om[10] + om[11])):
+        a = po.polarizability(M, Sig, tiny.mu, w)
+        b = po.polarizability_sum_over_states(om, res["X"], res["Y"], tiny.mu, w)
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-9 * np.abs(a).max())
+        np.testing.assert_allclose(a, a.T, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+        # the trace / 3 is sum_n f_n / (omega_n^2 - w^2)
+        assert np.trace(a) / 3 == pytest.approx(np.sum(res["f"] / (om ** 2 - w ** 2)), rel=1e-9)
+        if order == 0:
+            gap = (tiny.eps[None, o:] - tiny.eps[:o, None]).ravel()
+            m = tiny.mu.reshape(3, -1)
+            c = (m * (2 * gap / (gap ** 2 - w ** 2))[None, :]) @ m.T
+            np.testing.assert_allclose(a, c, rtol=1e-11, atol=1e-11 * np.abs(c).max())
