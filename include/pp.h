@@ -259,6 +259,16 @@ pp_status pp_last_stats(const pp_ctx *ctx, int *iterations, long long *sigma_vec
 pp_status pp_profile(pp_ctx *ctx, int enable);
 pp_status pp_profile_read(pp_ctx *ctx, int id, long long *launches, double *ms, double *flops);
 
+/*
+ * The tensor-core GEMM autotuner's table as text (one line per GEMM site and shape class:
+ * the chosen tile width, pipeline depth and K split, and the measured milliseconds of each
+ * tile configuration), preceded by the number of tunings run in this process.  Writes at most
+ * cap bytes (NUL-terminated) to buf and returns the size needed.  The tuner runs the first
+ * time a site meets a shape class; PP_AUTOTUNE=0 disables it, PP_TUNE_CACHE=<file> keeps the
+ * table in a text file across processes.
+ */
+long long pp_autotune_report(char *buf, long long cap);
+
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long pp_kernel_launches(void);
 

@@ -28,9 +28,10 @@ STATUS_NAMES = {
 # every symbol declared in include/pp.h
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
-    "pp_solve_windows", "pp_polarizability", "pp_spectrum", "pp_windows_begin", "pp_windows_step", "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_kernel_launches", "pp_destroy",
-    "pp_last_error", "pp_server_create", "pp_server_add_dot", "pp_server_submit", "pp_server_wait",
-    "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
+    "pp_solve_windows", "pp_polarizability", "pp_spectrum", "pp_windows_begin", "pp_windows_step",
+    "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_autotune_report",
+    "pp_kernel_launches", "pp_destroy", "pp_last_error", "pp_server_create", "pp_server_add_dot",
+    "pp_server_submit", "pp_server_wait", "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
 )
 
 
@@ -110,6 +111,8 @@ def load(path: str | None = None):
         lib.pp_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]
         lib.pp_profile_read.restype = C.c_int
+        lib.pp_autotune_report.argtypes = [C.c_char_p, C.c_longlong]
+        lib.pp_autotune_report.restype = C.c_longlong
         lib.pp_kernel_launches.argtypes = []
         lib.pp_kernel_launches.restype = C.c_longlong
         lib.pp_destroy.argtypes = [vp]
@@ -387,6 +390,15 @@ def pp_profile_read(ctx, kernel_id: int):
     fl = C.c_double()
     _check(lib.pp_profile_read(ctx, int(kernel_id), C.byref(n), C.byref(ms), C.byref(fl)), ctx)
     return dict(launches=n.value, ms=ms.value, flops=fl.value)
+
+
+def pp_autotune_report() -> str:
+    """The tensor-core GEMM autotuner's table (text)."""
+    lib = load()
+    n = int(lib.pp_autotune_report(None, 0))
+    buf = C.create_string_buffer(n)
+    lib.pp_autotune_report(buf, n)
+    return buf.value.decode(errors="replace")
 
 
 def pp_kernel_launches() -> int:

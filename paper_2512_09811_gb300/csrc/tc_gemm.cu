@@ -22,8 +22,13 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 namespace tc {
@@ -948,51 +953,219 @@ static CUtensorMap kmajor_map(const void *base, long long K, long long rows, lon
   return m;
 }
 
-// GEMM_STAGES for long reductions; GEMM_STAGES_SHORT (97 KB of shared memory) for GEMMs of a
-// few K steps, whose time goes to the epilogue: two CTAs then share an SM (their two 256-column
-// accumulators fill its TMEM), so one CTA's epilogue overlaps the other's main loop.
-constexpr int GEMM_BN = 256, GEMM_STAGES = 4, GEMM_STAGES_SHORT = 2, TGEN_STAGES = 3;
-constexpr int GEMM_SHORT_STEPS = 24;  // nseg * K / BK at or below which the short form is used
-constexpr size_t gemm_smem(int stages = GEMM_STAGES) {
-  return (size_t)stages * (BM * BK * 2 + GEMM_BN * BK * 2) + 1024;
-}
+// Tile configurations of k_gemm_bf16: (BN, stages) = (256, 4), 197 KB of shared memory, one
+// CTA per SM; (256, 2), 97 KB, two CTAs per SM (their two 256-column accumulators fill TMEM, so
+// one CTA's epilogue overlaps the other's main loop); (128, 6), 193 KB, one CTA per SM; (128, 3),
+// 97 KB, two CTAs per SM.  The autotuner below chooses among them per GEMM site and shape.
+struct GemmCfg {
+  int bn, stages;
+};
+// GEMM sites (the contractions the autotuner keys on)
+enum GemmSite { SITE_GAMMA = 0, SITE_U, SITE_W, SITE_KA, SITE_EF, SITE_KB, SITE_SLAB, SITE_SUMP1, SITE_SUMP2 };
+constexpr GemmCfg kGemmCfgs[] = {{256, 4}, {256, 2}, {128, 6}, {128, 3}};
+constexpr int NGEMMCFG = 4;
+constexpr int TGEN_STAGES = 3;
+constexpr int GEMM_SHORT_STEPS = 24;  // nseg * K / BK at or below which the default is the 2-CTA form
+constexpr size_t gemm_smem_cfg(int bn, int stages) { return (size_t)stages * (BM * BK * 2 + bn * BK * 2) + 1024; }
 constexpr size_t tgen_smem() { return (size_t)TGEN_STAGES * 4 * BM * BK * 2 + 1024; }
 
-// out (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K; output addressing per GemmOut
-void gemm_bf16(int M, int N, long long K, int nseg, const __nv_bfloat16 *const *A, long long lda,
-               const __nv_bfloat16 *const *B, long long ldb, const GemmOut &out, int *err, cudaStream_t s,
-               const GemmOut *out2 = nullptr) {
+template <int BN, int ST>
+static void launch_gemm_t(const GemmMaps &m, const GemmArgs &a, dim3 grid, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)gemm_smem()));
-    PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<GEMM_BN, GEMM_STAGES_SHORT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(GEMM_STAGES_SHORT)));
+    PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_smem_cfg(BN, ST)));
     attr = true;
   }
-  GemmMaps maps;
-  std::memset(&maps, 0, sizeof(maps));
-  for (int g = 0; g < nseg; ++g) {
-    maps.a[g] = kmajor_map(A[g], K, M, lda, BM);
-    maps.b[g] = kmajor_map(B[g], K, N, ldb, GEMM_BN);
-  }
-  GemmArgs a{M, N, (int)(K / BK), nseg, out, out2 ? *out2 : GemmOut{}, err};
-  dim3 grid((M + BM - 1) / BM, (N + GEMM_BN - 1) / GEMM_BN);
-  // few output tiles over a long reduction (an accumulating FP32 output): split K across
-  // CTAs so that about two waves of the GPU share it, each taking at least 8 K steps
-  if (out.C && out.accumulate && !out2) {
-    const long long tiles = (long long)grid.x * grid.y, steps = (long long)nseg * a.nk;
-    long long ks = std::min<long long>(304 / std::max<long long>(tiles, 1), steps / 8);
-    ks = std::max<long long>(1, std::min<long long>(ks, 65535));
-    a.ksplit = (int)ks;
-    grid.z = (unsigned)ks;
-  }
-  if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
-  if (a.ksplit == 1 && (long long)nseg * a.nk <= GEMM_SHORT_STEPS)
-    k_gemm_bf16<GEMM_BN, GEMM_STAGES_SHORT><<<grid, 128, gemm_smem(GEMM_STAGES_SHORT), s>>>(maps, a);
-  else
-    k_gemm_bf16<GEMM_BN, GEMM_STAGES><<<grid, 128, gemm_smem(), s>>>(maps, a);
+  k_gemm_bf16<BN, ST><<<grid, 128, gemm_smem_cfg(BN, ST), s>>>(m, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
+}
+static void launch_gemm_cfg(int cfg, const GemmMaps &m, const GemmArgs &a, dim3 grid, cudaStream_t s) {
+  switch (cfg) {
+    case 0: launch_gemm_t<256, 4>(m, a, grid, s); break;
+    case 1: launch_gemm_t<256, 2>(m, a, grid, s); break;
+    case 2: launch_gemm_t<128, 6>(m, a, grid, s); break;
+    default: launch_gemm_t<128, 3>(m, a, grid, s); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the tensor-core GEMMs.  The first time a GEMM site meets a shape class
+// (octaves of M, N and K, the number of split segments, whether the output accumulates), it
+// runs every tile configuration -- and, for accumulating outputs, the K-split the default rule
+// picks and no split -- twice, timed with CUDA events on the launching stream, keeps the
+// fastest, and reruns it for the result.  GEMMs whose output is overwritten are idempotent; an
+// accumulating output is copied aside before the first candidate and restored before each run.
+// The choices live in a process-wide table (pp_autotune_report prints it).  PP_AUTOTUNE=0 turns
+// tuning off (the default rule below is then used everywhere); PP_TUNE_CACHE=<file> loads the
+// table from, and appends new entries to, a text file.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int site, nseg, acc, dev, m, n, k;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(site, nseg, acc, dev, m, n, k) < std::tie(o.site, o.nseg, o.acc, o.dev, o.m, o.n, o.k);
+  }
+};
+struct TuneVal {
+  int cfg = 0, ksplit = 1;
+  float ms[2 * NGEMMCFG] = {0};  // measured time of each candidate (cfg, split choice)
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+static long long g_tune_runs = 0;  // tunings performed in this process
+static bool g_tune_init = false, g_tune_on = true;
+static std::string g_tune_file;
+static const char *kSiteName[] = {"gamma", "U", "W", "KA", "EF", "KB", "slab", "sumP1", "sumP2", "other"};
+
+static int octave(long long x) {
+  int b = 0;
+  while ((1LL << b) < x && b < 62) ++b;
+  return b;
+}
+static void tune_init_locked() {
+  if (g_tune_init) return;
+  g_tune_init = true;
+  const char *e = std::getenv("PP_AUTOTUNE");
+  g_tune_on = !(e && e[0] == '0');
+  const char *f = std::getenv("PP_TUNE_CACHE");
+  if (f && f[0]) {
+    g_tune_file = f;
+    if (FILE *fp = std::fopen(f, "r")) {
+      TuneKey k;
+      TuneVal v;
+      while (std::fscanf(fp, "%d %d %d %d %d %d %d %d %d", &k.site, &k.nseg, &k.acc, &k.dev, &k.m, &k.n, &k.k,
+                         &v.cfg, &v.ksplit) == 9)
+        if (v.cfg >= 0 && v.cfg < NGEMMCFG && v.ksplit >= 1) g_tune[k] = v;
+      std::fclose(fp);
+    }
+  }
+}
+
+// default K split of an accumulating output: about two waves of CTAs over few output tiles,
+// each CTA taking at least 8 K steps
+static int default_ksplit(long long tiles, long long steps) {
+  long long ks = std::min<long long>(304 / std::max<long long>(tiles, 1), steps / 8);
+  return (int)std::max<long long>(1, std::min<long long>(ks, 65535));
+}
+
+// out (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K; output addressing per GemmOut.
+// site names the contraction for the autotuner; acc_base / acc_bytes give the region an
+// accumulating output writes (restored between tuning runs; without it such a GEMM is not tuned).
+void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat16 *const *A, long long lda,
+               const __nv_bfloat16 *const *B, long long ldb, const GemmOut &out, int *err, cudaStream_t s,
+               const GemmOut *out2 = nullptr, void *acc_base = nullptr, size_t acc_bytes = 0) {
+  GemmMaps maps[2];  // B boxes of 256 and 128 rows
+  bool built[2] = {false, false};
+  auto maps_for = [&](int bn) -> const GemmMaps & {
+    const int w = bn == 256 ? 0 : 1;
+    if (!built[w]) {
+      std::memset(&maps[w], 0, sizeof(GemmMaps));
+      for (int g = 0; g < nseg; ++g) {
+        maps[w].a[g] = kmajor_map(A[g], K, M, lda, BM);
+        maps[w].b[g] = kmajor_map(B[g], K, N, ldb, bn);
+      }
+      built[w] = true;
+    }
+    return maps[w];
+  };
+  const bool acc = out.C && out.accumulate && !out2;
+  const int nk = (int)(K / BK);
+  auto args_for = [&](int bn, int ksplit, dim3 &grid) {
+    GemmArgs a{M, N, nk, nseg, out, out2 ? *out2 : GemmOut{}, err};
+    grid = dim3((M + BM - 1) / BM, (N + bn - 1) / bn, 1);
+    if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
+    a.ksplit = ksplit;
+    grid.z = (unsigned)ksplit;
+    return a;
+  };
+  auto ks_for = [&](int bn) {
+    if (!acc) return 1;
+    const long long tiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn);
+    return default_ksplit(tiles, (long long)nseg * nk);
+  };
+  auto run = [&](int cfg, int ksplit) {
+    dim3 grid;
+    const int bn = kGemmCfgs[cfg].bn;
+    GemmArgs a = args_for(bn, ksplit, grid);
+    launch_gemm_cfg(cfg, maps_for(bn), a, grid, s);
+  };
+  int dev = 0;
+  PP_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{site, nseg, acc ? 1 : 0, dev, octave(M), octave(N), octave(K)};
+  TuneVal chosen;
+  bool have = false, tune = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_init_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      chosen = it->second;
+      have = true;
+    } else {
+      tune = g_tune_on && (!acc || (acc_base && acc_bytes));
+    }
+  }
+  if (have) {
+    // a stored K split larger than the reduction allows falls back to the default rule
+    const int ks = (chosen.ksplit > 1 && (long long)chosen.ksplit * 8 > (long long)nseg * nk) ? ks_for(kGemmCfgs[chosen.cfg].bn)
+                                                                                             : chosen.ksplit;
+    run(chosen.cfg, acc ? ks : 1);
+    return;
+  }
+  if (!tune) {  // the default rule
+    const int ks = ks_for(256);
+    run((ks == 1 && (long long)nseg * nk <= GEMM_SHORT_STEPS) ? 1 : 0, ks);
+    return;
+  }
+  // tune: every configuration (and for accumulating outputs the default split and none)
+  DevBuf snap;
+  if (acc) {
+    snap.ensure(acc_bytes);
+    PP_CUDA(cudaMemcpyAsync(snap.p, acc_base, acc_bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  cudaEvent_t e0, e1;
+  PP_CUDA(cudaEventCreate(&e0));
+  PP_CUDA(cudaEventCreate(&e1));
+  TuneVal best;
+  float best_ms = 1e30f;
+  for (int cfg = 0; cfg < NGEMMCFG; ++cfg) {
+    const int ksd = ks_for(kGemmCfgs[cfg].bn);
+    const int nsplit = (acc && ksd > 1) ? 2 : 1;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const int ks = sp == 0 ? ksd : 1;
+      float t = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (acc) PP_CUDA(cudaMemcpyAsync(acc_base, snap.p, acc_bytes, cudaMemcpyDeviceToDevice, s));
+        PP_CUDA(cudaEventRecord(e0, s));
+        run(cfg, ks);
+        PP_CUDA(cudaEventRecord(e1, s));
+        PP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t = std::min(t, ms);
+      }
+      best.ms[2 * cfg + sp] = t;
+      if (t < best_ms) {
+        best_ms = t;
+        best.cfg = cfg;
+        best.ksplit = ks;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (acc) PP_CUDA(cudaMemcpyAsync(acc_base, snap.p, acc_bytes, cudaMemcpyDeviceToDevice, s));
+  run(best.cfg, best.ksplit);
+  PP_CUDA(cudaStreamSynchronize(s));  // the snapshot is freed on return
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  ++g_tune_runs;
+  if (!g_tune_file.empty())
+    if (FILE *fp = std::fopen(g_tune_file.c_str(), "a")) {
+      std::fprintf(fp, "%d %d %d %d %d %d %d %d %d\n", key.site, key.nseg, key.acc, key.dev, key.m, key.n, key.k,
+                   best.cfg, best.ksplit);
+      std::fclose(fp);
+    }
 }
 
 void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq, long long ov, int o, int v,
@@ -1357,7 +1530,7 @@ void precompute_tc(pp_ctx *c) {
       out.C = gam + (long long)i0 * v;
       out.s_r0 = 1;
       out.s_c0 = ov;
-      tc::gemm_bf16((int)rows, Q, ldT, 3, A, ldT, B, ldT, out, err, s);
+      tc::gemm_bf16(tc::SITE_GAMMA, (int)rows, Q, ldT, 3, A, ldT, B, ldT, out, err, s);
     }
     const float *src[5] = {poo, qoo, pvv, qvv, gam};
     double *dst[5] = {c->p_oo.as<double>(), c->q_oo.as<double>(), c->p_vv.as<double>(), c->q_vv.as<double>(),
@@ -1495,7 +1668,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         ku.d_c = v;
         ku.s_c1 = (long long)o * kqv;
         ku.s_c0 = 1;
-        tc::gemm_bf16(Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, ku, err, s);
+        tc::gemm_bf16(tc::SITE_U, Q * o, Rc * v, kbo, nseg1, A, kbo, B, kbo, ku, err, s);
       }
       // W[r][j][Q][d] = sum_b V[r][j][b] Bvv[Q][b][d]: rows (r,j), columns (Q,d), written as
       // C_Q(V) = W - U (BF16 pair, [(r,Q)][(j,d)]) for the amplitude contraction; U[r][Q][j][d]
@@ -1515,7 +1688,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         cc.add_lo = kul;
         cc.add_ld = kqv;
         cc.add_scale = -1.f;
-        tc::gemm_bf16(Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s);
+        tc::gemm_bf16(tc::SITE_W, Rc * o, Q * v, vp, nseg1, A, vp, B, vp, cc, err, s);
       }
       // KA: Aacc[r][i][a] -= sum_(Q,k) Boo[Q][i][k] W[r][k][Q][a] = sum_(Q,b) U[r][Q][i][b] Bvv[Q][b][a]
       // (rows (r,i), columns a, K = (Q,b))
@@ -1527,7 +1700,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.s_c0 = 1;
         out.alpha = -1.f;
         out.accumulate = 1;
-        tc::gemm_bf16(Rc * o, v, kqv, nseg1, A, kqv, B, kqv, out, err, s);
+        tc::gemm_bf16(tc::SITE_KA, Rc * o, v, kqv, nseg1, A, kqv, B, kqv, out, err, s, nullptr, Aacc,
+                      sizeof(float) * (size_t)Rc * ov);
       }
       if (tda) return true;
       // E and F: EF[(r,i)][(t,j)] = sum_b X_t[i][b] V[r][j][b], X = Bov (t < Q), Gamma (t >= Q)
@@ -1542,12 +1716,12 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.s_c1 = (long long)o * kef;
         out.s_c0 = 1;
         seg3(p->bov_hi.as<bf>(), p->bov_lo.as<bf>(), vhi, vlo, A, B);
-        tc::gemm_bf16(Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
+        tc::gemm_bf16(tc::SITE_EF, Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
         if (order >= 2) {
           out.Chi = efh + (long long)Q * o;
           out.Clo = efl ? efl + (long long)Q * o : nullptr;
           seg3(p->gam_hi.as<bf>(), p->gam_lo.as<bf>(), vhi, vlo, A, B);
-          tc::gemm_bf16(Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
+          tc::gemm_bf16(tc::SITE_EF, Q * o, Rc * o, vp, nseg1, A, vp, B, vp, out, err, s);
         }
       }
       // KB: Bacc[r][i][a] -= sum_(t,j) EF[r][t][i][j] GB[t][j][a]   (rows (r,i), columns a)
@@ -1558,7 +1732,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.s_r0 = v;
         out.alpha = -1.f;
         out.accumulate = 1;
-        tc::gemm_bf16(Rc * o, v, kef, nseg1, A, kef, B, kef, out, err, s);
+        tc::gemm_bf16(tc::SITE_KB, Rc * o, v, kef, nseg1, A, kef, B, kef, out, err, s, nullptr, Bacc,
+                      sizeof(float) * (size_t)Rc * ov);
       }
       return true;
     };
@@ -1608,7 +1783,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         o2.s_c1 = ov * Qp;
         prof_mark(p->prof, 0, s);
         if (split) prof_mark(p->prof, 2, s);
-        tc::gemm_bf16((int)rows, (int)NC, ldT, nseg, A, ldT, B, ldT, o1, err, s, &o2);
+        tc::gemm_bf16(tc::SITE_SLAB, (int)rows, (int)NC, ldT, nseg, A, ldT, B, ldT, o1, err, s, &o2);
         prof_mark(p->prof, 0, s);
         if (split) prof_mark(p->prof, 2, s);
         if (p->prof.on) {  // algorithmic: the contraction once (the split form's three
@@ -1628,7 +1803,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.C = Bacc;
         out.s_r0 = v;
         out.accumulate = 1;
-        tc::gemm_bf16(Rc * o, v, (long long)v * Qp, nseg, A, (long long)v * Qp, B, (long long)v * Qp, out, err, s);
+        tc::gemm_bf16(tc::SITE_SUMP1, Rc * o, v, (long long)v * Qp, nseg, A, (long long)v * Qp, B, (long long)v * Qp,
+                      out, err, s, nullptr, Bacc, sizeof(float) * (size_t)Rc * ov);
       }
       // Bacc[r][i][a] -= sum_(k,q) P2[(r,a)][(k,q)] Boo[q][i][k]   (rows (r,a), columns i)
       {
@@ -1642,8 +1818,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
         out.s_c0 = v;
         out.alpha = -1.f;
         out.accumulate = 1;
-        tc::gemm_bf16(Rc * v, o, (long long)o * Qp, nseg, A, (long long)o * Qp, B, (long long)o * Qp, out, err,
-                      s);
+        tc::gemm_bf16(tc::SITE_SUMP2, Rc * v, o, (long long)o * Qp, nseg, A, (long long)o * Qp, B,
+                      (long long)o * Qp, out, err, s, nullptr, Bacc, sizeof(float) * (size_t)Rc * ov);
       }
     };
     sigma_chunk<float>(c, R, V, V64, sig_d + (long long)r0 * ov, met_d ? met_d + (long long)r0 * ov : nullptr,
@@ -1661,6 +1837,34 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
 // ---------------------------------------------------------------------------
 // profiling entry points (C ABI)
 // ---------------------------------------------------------------------------
+extern "C" long long pp_autotune_report(char *buf, long long cap) {
+  std::string r;
+  {
+    std::lock_guard<std::mutex> lk(tc::g_tune_mu);
+    tc::tune_init_locked();
+    r += "autotune " + std::string(tc::g_tune_on ? "on" : "off") + ", tunings " + std::to_string(tc::g_tune_runs) + "\n";
+    for (const auto &kv : tc::g_tune) {
+      const tc::TuneKey &k = kv.first;
+      const tc::TuneVal &v = kv.second;
+      char line[256];
+      std::snprintf(line, sizeof(line), "%s nseg=%d acc=%d M~2^%d N~2^%d K~2^%d -> BN=%d stages=%d ksplit=%d |",
+                    tc::kSiteName[std::min(k.site, 9)], k.nseg, k.acc, k.m, k.n, k.k, tc::kGemmCfgs[v.cfg].bn,
+                    tc::kGemmCfgs[v.cfg].stages, v.ksplit);
+      r += line;
+      for (int c = 0; c < tc::NGEMMCFG; ++c) {
+        std::snprintf(line, sizeof(line), " %.3f", v.ms[2 * c]);
+        r += line;
+      }
+      r += " ms\n";
+    }
+  }
+  if (buf && cap > 0) {
+    const long long n = std::min<long long>(cap - 1, (long long)r.size());
+    std::memcpy(buf, r.data(), (size_t)n);
+    buf[n] = 0;
+  }
+  return (long long)r.size() + 1;
+}
 extern "C" pp_status pp_profile(pp_ctx *c, int enable) {
   if (!c) return PP_EINVAL;
   try {
