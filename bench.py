@@ -203,7 +203,7 @@ def run_ours(args, world, rank, local):
     o, v, Q = w["nocc"], w["nvir"], w["naux"]
     inp = make_dot_inputs(w)
     opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"], refine=1,
-                  max_iter=300, cuda_stream=stream.cuda_stream)
+                  max_iter=300, cuda_stream=stream.cuda_stream, workspace_gb=args.workspace_gb)
     t0 = time.time()
     dot = pp.Dot(inp, **opt_kw)
     torch.cuda.synchronize()
@@ -267,22 +267,28 @@ def run_ours(args, world, rank, local):
     ms_max, flops_tot = reduce_over_ranks(dist, timed_ms, timed_flops, "cuda")
     value = flops_tot / (ms_max / 1e3) / 1e12
     # finish the solve that was running when the timed steps ended (at least one full batch)
-    while not solves:
-        one_step()
-    first = solves[0]
-    solve_ms_max, roots_tot = reduce_over_ranks(dist, first["ms"], first["roots"], "cuda")
-    roots_per_s = roots_tot / (solve_ms_max / 1e3)
-    solve_flops = first["sigma_vectors"] * sigma_flops_per_vector(o, v, Q)
+    roots_obj = None
+    if not args.no_full_solve:
+        while not solves:
+            one_step()
+        first = solves[0]
+        solve_ms_max, roots_tot = reduce_over_ranks(dist, first["ms"], first["roots"], "cuda")
+        solve_flops = first["sigma_vectors"] * sigma_flops_per_vector(o, v, Q)
+        roots_obj = dict(roots_per_s=roots_tot / (solve_ms_max / 1e3), roots=int(roots_tot),
+                         solve_s=solve_ms_max / 1e3, iterations=first["iterations"],
+                         sigma_vectors=first["sigma_vectors"], max_resid=first["max_resid"], found=first["found"],
+                         status=first["status"], sigma_tflops=solve_flops / (first["ms"] / 1e3) / 1e12)
 
     # ---- end to end through the C ABI from pinned host buffers ---------------------------
     from synth.inputs import DotInputs
 
-    pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(inp, f))).pin_memory().numpy() for f in ("eps", "B", "mu")}
-    pinned = DotInputs(nocc=inp.nocc, nvir=inp.nvir, naux=inp.naux, sigma_b=inp.sigma_b, seed=inp.seed, **pin)
     h2d = inp.eps.nbytes + inp.B.nbytes + inp.mu.nbytes
     d2h = sum(ks) * 3 * 8 + 4 * len(ks)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.no_full_solve:
+        pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(inp, f))).pin_memory().numpy()
+               for f in ("eps", "B", "mu")}
+        pinned = DotInputs(nocc=inp.nocc, nvir=inp.nvir, naux=inp.naux, sigma_b=inp.sigma_b, seed=inp.seed, **pin)
         dot.close()
         torch.cuda.synchronize()
         t0 = time.time()
@@ -329,10 +335,7 @@ def run_ours(args, world, rank, local):
                     inputs=w["mode"], step="one block iteration of all windows (pp_windows_step)",
                     l2="inputs larger than L2 (FP32 B tensor %.1f GB; slab and operands > 129 MB)" % (inp.B.nbytes / 1e9),
                     parallelism=f"replicas{world}"),
-        roots=dict(roots_per_s=roots_per_s, roots=int(roots_tot), solve_s=solve_ms_max / 1e3,
-                   iterations=first["iterations"], sigma_vectors=first["sigma_vectors"],
-                   max_resid=first["max_resid"], found=first["found"], status=first["status"],
-                   sigma_tflops=solve_flops / (first["ms"] / 1e3) / 1e12),
+        roots=roots_obj,
         roofline=roof,
         e2e=e2e,
         gpu_launches=int(launches),
@@ -432,13 +435,15 @@ def serving_leg(args):
         st = srv.stats()
     finally:
         srv.close()
+    served = roots / finish
     return dict(requests=n_req, arrival_rate_per_s=rate, arrivals_s=reqs[-1][0], sizes=[list(z) for z in sizes],
+                regime="sustained" if reqs[-1][0] >= 0.5 * finish else "burst (arrivals end before half the drain)",
                 dots_per_size=4, k_choices=[4, 8, 16], window_ha=[0.05, 0.2],
                 start="U[pct10, pct50] of diag(A)/diag(S)",
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 p50_ms_by_size={str(list(sizes[s])): float(np.percentile(v_, 50)) for s, v_ in by_size.items() if v_},
                 p99_ms_by_size={str(list(sizes[s])): float(np.percentile(v_, 99)) for s, v_ in by_size.items() if v_},
-                roots_per_s=roots / finish, roots=roots, wall_s=finish, not_converged=notconv,
+                roots_per_s=served, roots=roots, wall_s=finish, not_converged=notconv,
                 slots_per_dot=4, workers=4, max_concurrent_dots=st["max_concurrent_dots"],
                 max_windows_per_step=st["max_windows_per_step"], ctx_created=st["ctx_created"],
                 ctx_evicted=st["ctx_evicted"], failed=st["failed"])
@@ -551,6 +556,11 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve from host buffers")
+    ap.add_argument("--no-full-solve", action="store_true",
+                    help="time the steps only, without finishing the solve (the large dot: a full solve takes "
+                         "tens of minutes)")
+    ap.add_argument("--workspace-gb", type=float, default=0.0,
+                    help="device memory for one chunk of the sigma workspaces (0: automatic)")
     ap.add_argument("--fp64-leg", action="store_true",
                     help="also solve the 64/256/768 window in the plain FP64 form and the mixed form "
                          "(minutes: the FP64 form issues at GB300's FP64 rate)")

@@ -177,6 +177,22 @@ pp_status pp_solve_window(pp_ctx *ctx, double omega0, double delta, int k, doubl
                           double *osc, double *resid, double *vecs, int *nfound);
 
 /*
+ * All roots inside [omega0, omega0 + delta] by the contour filter of Sec. 4.4 (the Riesz
+ * projector, the alternative interior method the paper names): the projector onto the roots
+ * inside the circle through omega0 and omega0 + delta is applied to a block of trial vectors
+ * with nquad trapezoidal points on the circle (complex shifted systems solved by conjugate-
+ * orthogonal CG with the Jacobi diagonal), followed by Rayleigh-Ritz with the accurate sigma,
+ * repeated until every Ritz pair in the window meets res_tol (at most min(max_iter, 60)
+ * filter applications).  The block holds 1.5 times the diagonal's count of roots in the window
+ * plus 4, at most 64 vectors (PP_EINVAL for wider windows).  Mixed contexts filter with the
+ * BF16 sigma and take Rayleigh-Ritz products with the split form.
+ *   omega, osc, resid: host outputs of capacity k, ascending; *nfound: the roots in the window
+ *   (PP_EINVAL if more than k).  PP_ENOTCONV with the last estimates if the limit is reached.
+ */
+pp_status pp_solve_window_contour(pp_ctx *ctx, double omega0, double delta, int nquad, int k, double *omega,
+                                  double *osc, double *resid, int *nfound);
+
+/*
  * Several windows of one dot solved together: all windows' trial blocks go
  * through one sigma batch per iteration.  Outputs are concatenated per window
  * at offsets off[w] = sum_{u<w} k[u]; nfound[nwin].

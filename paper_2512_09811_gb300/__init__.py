@@ -28,7 +28,7 @@ STATUS_NAMES = {
 # every symbol declared in include/pp.h
 EXPORTS = (
     "pp_default_options", "pp_create", "pp_sigma", "pp_metric_noalloc", "pp_diagonal", "pp_solve_window",
-    "pp_solve_windows", "pp_polarizability", "pp_spectrum", "pp_windows_begin", "pp_windows_step",
+    "pp_solve_windows", "pp_solve_window_contour", "pp_polarizability", "pp_spectrum", "pp_windows_begin", "pp_windows_step",
     "pp_windows_end", "pp_last_stats", "pp_profile", "pp_profile_read", "pp_autotune_report",
     "pp_kernel_launches", "pp_destroy", "pp_last_error", "pp_server_create", "pp_server_add_dot",
     "pp_server_submit", "pp_server_wait", "pp_server_stats", "pp_server_last_error", "pp_server_destroy",
@@ -92,6 +92,9 @@ def load(path: str | None = None):
         lib.pp_solve_windows.argtypes = [vp, C.c_int, _dp, _dp, C.POINTER(C.c_int), _dp, _dp, _dp,
                                          C.POINTER(C.c_int)]
         lib.pp_solve_windows.restype = C.c_int
+        lib.pp_solve_window_contour.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp, _dp,
+                                                C.POINTER(C.c_int)]
+        lib.pp_solve_window_contour.restype = C.c_int
         lib.pp_polarizability.argtypes = [vp, C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
         lib.pp_polarizability.restype = C.c_int
         lib.pp_spectrum.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp,
@@ -297,6 +300,21 @@ def pp_solve_windows(ctx, omega0, delta, k, allow_notconv: bool = False):
     return out, st
 
 
+def pp_solve_window_contour(ctx, omega0: float, delta: float, k: int, nquad: int = 8, allow_notconv: bool = False):
+    """All roots in [omega0, omega0 + delta] by the contour (Riesz projector) filter."""
+    lib = load()
+    om = np.zeros(k)
+    osc = np.zeros(k)
+    res = np.zeros(k)
+    nf = C.c_int(0)
+    st = lib.pp_solve_window_contour(ctx, float(omega0), float(delta), int(nquad), int(k), _ptr(om), _ptr(osc),
+                                     _ptr(res), C.byref(nf))
+    if not (allow_notconv and st == PP_ENOTCONV):
+        _check(st, ctx)
+    n = nf.value
+    return dict(omega=om[:n], osc=osc[:n], resid=res[:n], status=st)
+
+
 def pp_polarizability(ctx, omega, tol: float = 1e-8, max_iter: int = 2000, allow_notconv: bool = False):
     """Dipole polarizability alpha[f][c][c'] at real frequencies: dict(alpha, resid, iterations, status)."""
     lib = load()
@@ -439,6 +457,9 @@ class Dot:
 
     def windows(self, omega0, delta, k):
         return WindowRun(self.ctx, omega0, delta, k)
+
+    def solve_window_contour(self, omega0, delta, k, **kw):
+        return pp_solve_window_contour(self.ctx, omega0, delta, k, **kw)
 
     def polarizability(self, omega, **kw):
         return pp_polarizability(self.ctx, omega, **kw)

@@ -271,6 +271,27 @@ extern "C" pp_status pp_solve_windows(pp_ctx *c, int nwin, const double *omega0,
   });
 }
 
+extern "C" pp_status pp_solve_window_contour(pp_ctx *c, double omega0, double delta, int nquad, int k, double *omega,
+                                             double *osc, double *resid, int *nfound) {
+  if (!c) return PP_EINVAL;
+  if (!std::isfinite(omega0) || !(delta > 0) || nquad < 2 || nquad > 32 || k < 1 || !omega || !osc || !resid ||
+      !nfound) {
+    c->err = "pp_solve_window_contour: bad argument";
+    return PP_EINVAL;
+  }
+  return guarded(c, [&]() -> pp_status {
+    PP_CUDA(cudaEventRecord(c->ev0, c->stream));
+    const int outer = std::max(1, std::min(c->opt.max_iter, 60));
+    pp_status st = riesz_impl(c, omega0, delta, nquad, 0, outer, omega, osc, resid, k, nfound);
+    PP_CUDA(cudaEventRecord(c->ev1, c->stream));
+    PP_CUDA(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    PP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->st_solve_ms = ms;
+    return st;
+  });
+}
+
 extern "C" pp_status pp_polarizability(pp_ctx *c, int nfreq, const double *omega, double tol, int max_iter,
                                        double *alpha, double *resid, int *iterations) {
   if (!c) return PP_EINVAL;

@@ -160,6 +160,7 @@ struct pp_ctx {
 
 // sigma_f64.cu
 void build_residency(pp_ctx *c, const double *Bd, const float *Bf);
+void ensure_bvvp(pp_ctx *c);  // the permuted FP64 Bvv of the FP64 sigma (built on first use)
 // per-dot intermediates (MP2 pair sums p_oo, q_oo, p_vv, q_vv, ring intermediate Gamma, then
 // GB and the Jacobi diagonal): precompute_f64 in FP64; precompute_tc on the tensor cores
 // (split-BF16 amplitude slabs and Gamma, FP32 pair sums), both via begin / finish
@@ -200,6 +201,9 @@ void window_run_destroy(pp_ctx *c);
 pp_status spectrum_impl(pp_ctx *c, double w_lo, double w_hi, int nwin, int kmax, double eta, int ngrid,
                         const double *grid, double *spec, int cap, double *omega, double *osc, double *resid,
                         int *nroots);
+// contour (Riesz projector) filter solver of one window (solver.cu)
+pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0, int max_outer, double *omega,
+                     double *osc, double *resid, int cap, int *nfound);
 // frequency-dependent dipole polarizability by preconditioned MINRES (response.cu)
 pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double tol, int max_iter, double *alpha,
                               double *resid, int *iterations);

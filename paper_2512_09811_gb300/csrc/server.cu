@@ -64,15 +64,17 @@ struct SrvDot {
 size_t estimate_bytes(long long o, long long v, long long Q, const pp_options &opt, int slots) {
   const long long ov = o * v, n = o + v, L = 2 * ov;
   auto pad = [](long long x) { return std::max<long long>(64, (x + 63) / 64 * 64); };
-  long long total = 8 * (Q * (o * o + ov + v * v) + Q * (v * v + o * o) + 3 * Q * ov + 8 * ov + 2 * o * o +
-                         2 * v * v + n);
+  // FP64 blocks Boo, Bov, Bvv, BooT, GB, Gamma and the small intermediates; the permuted Bvv
+  // only in the FP64 form
+  long long total = 8 * (Q * (o * o + ov + v * v) + Q * o * o + 3 * Q * ov + 8 * ov + 2 * o * o + 2 * v * v + n);
+  if (opt.prec == PP_FP64) total += 8 * Q * v * v;
   const long long rows_max = 2LL * 32 * slots;  // half-vectors of the largest step batch
   if (opt.prec != PP_FP64) {
     const long long ldq = pad(Q), ldT = pad(ov), vp = pad(v), Qp = pad(Q);
-    total += 4 * (ov + n + Q * ov + 2 * Q * o * o + 2 * Q * v * v + 3 * Q * ov + 2 * o * o + 2 * v * v);
+    total += 4 * (n + Q * ov + 2 * o * o + 2 * v * v);  // FP32 eps, Bov and pair sums
     total += 4 * (ov * ldq + Q * v * vp + 2 * Q * o * vp + v * v * Qp + o * o * Qp + v * pad(Q * v));
-    const long long per_half =
-        4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 4 * Q * ldT + 8 * ov * Qp + 4 * o * pad(Q * v);
+    const long long per_half = 4 * (7 * ov + Q) + 4 * (o * vp + v * pad(o) + o * pad(Q * v) + o * pad(2 * Q * o)) +
+                               4 * Q * ldT + 8 * ov * Qp;
     const long long ws = (long long)(opt.workspace_gb * (1LL << 30));
     long long R = std::max<long long>(2, std::min<long long>(ws / std::max<long long>(per_half, 1), 64));
     R = std::min(R & ~1LL, rows_max);

@@ -168,13 +168,24 @@ void build_residency(pp_ctx *c, const double *Bd, const float *Bf) {
     k_extract_blocks_f32<<<ew_grid(total), 256, 0, s>>>(Bf, n, o, v, Q, c->Boo.as<double>(),
                                                         c->Bov.as<double>(), c->Bvv.as<double>());
   PP_LAUNCH_CHECK("k_extract_blocks");
-  c->BvvP.ensure(sizeof(double) * (size_t)Q * v * v);
-  k_perm_bvv<<<ew_grid((long long)Q * v * v), 256, 0, s>>>(c->Bvv.as<double>(), c->BvvP.as<double>(), v, Q);
+  // the permuted copy of Bvv serves only the FP64 sigma: contexts of the mixed form build it at
+  // their first FP64 sigma (it is as large as Bvv itself)
+  if (c->opt.prec == PP_FP64) ensure_bvvp(c);
   c->BooT.ensure(sizeof(double) * (size_t)Q * o * o);
   k_perm_boo<<<ew_grid((long long)Q * o * o), 256, 0, s>>>(c->Boo.as<double>(), c->BooT.as<double>(), o, Q);
   c->gap.ensure(sizeof(double) * (size_t)o * v);
   k_gap<<<(o * v + 255) / 256, 256, 0, s>>>(c->eps.as<double>(), c->gap.as<double>(), o, v);
   PP_LAUNCH_CHECK("residency");
+}
+
+void ensure_bvvp(pp_ctx *c) {
+  const long long total = (long long)c->Q * c->v * c->v;
+  if (c->BvvP.bytes >= sizeof(double) * (size_t)std::max<long long>(total, 1)) return;
+  c->BvvP.ensure(sizeof(double) * (size_t)std::max<long long>(total, 1));
+  if (total > 0) {
+    k_perm_bvv<<<ew_grid(total), 256, 0, c->stream>>>(c->Bvv.as<double>(), c->BvvP.as<double>(), c->v, c->Q);
+    PP_LAUNCH_CHECK("k_perm_bvv");
+  }
 }
 
 static void choose_chunks(pp_ctx *c) {
@@ -283,6 +294,7 @@ void precompute_finish(pp_ctx *c) {
 void sigma_f64(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d) {
   const int o = c->o, v = c->v, Q = c->Q;
   const long long ov = c->ov;
+  if (c->opt.order >= 1) ensure_bvvp(c);
   const int Rmax = c->sig_chunk;
   c->w_acc.ensure(sizeof(double) * 2 * (size_t)Rmax * ov);
   c->w_tmp.ensure(sizeof(double) * 4 * (size_t)Rmax * ov);

@@ -167,6 +167,8 @@ void sigma_chunk(const pp_ctx *c, int R, const T *V, const double *V64, double *
     if (hk.first_order && hk.first_order(R, Aacc, Bacc)) {
       if (order >= 2 && !tda) hk.amplitude(R, nullptr, Bacc);
     } else {
+      if (!res.Boo || !res.Bvv || !res.BvvP || !res.GB || !res.Gam)
+        throw PPError(PP_ECUDA, "sigma: step-by-step contractions need operands this form does not keep");
       T *W = wk.W;  // W[r][j][Q][d] = V_r BvvP
       const long long oQv = (long long)o * Q * v;
       if (!(hk.w && hk.w(R, V, W))) {

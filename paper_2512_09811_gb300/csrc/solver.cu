@@ -2034,3 +2034,424 @@ pp_status windows_end(pp_ctx *c, double *omega_out, double *osc_out, double *res
   c->run = nullptr;
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Contour (Riesz projector) solver, the alternative interior method of Sec. 4.4.
+//
+// The Riesz projector of the pencil onto the roots inside a circle Gamma around the window,
+//   P = (1 / 2 pi i) oint_Gamma (z Sigma - M)^-1 Sigma dz,
+// is applied to a block Y of m0 trial vectors with the trapezoidal rule on the circle
+// z(theta) = c + rho e^{i theta}, c the window centre, rho half its width.  Conjugate points
+// give conjugate solutions (M and Sigma are real), so with Nq points on the upper half,
+//   P Y ~ (1 / Nq) Re sum_j rho e^{i theta_j} X_j,   (z_j Sigma - M) X_j = Sigma Y,
+//   theta_j = pi (j + 1/2) / Nq,
+// whose scalar filter is 1 at the centre and decays away from the circle.  Each complex
+// system is complex symmetric; all Nq m0 of them are solved together by conjugate-orthogonal
+// CG (unconjugated inner products) with the diagonal preconditioner diag(z_j Sigma - M), one
+// sigma batch of their real and imaginary parts per iteration.  The filtered block is
+// orthonormalised, multiplied with the accurate sigma and Rayleigh-Ritz'd (the projected
+// pencil as in the window solver); the Ritz vectors are filtered again until every Ritz
+// pair inside the window meets the tolerance (subspace iteration with a rational filter).
+// Mixed contexts filter with the BF16 sigma (the filter's accuracy sets only the convergence
+// rate) and take the Rayleigh-Ritz products and residuals with the split form.
+// ---------------------------------------------------------------------------
+namespace {
+
+// per system s (complex vector s = real parts at 2s, imaginary parts at 2s + 1, each L long)
+struct RzCoef {
+  const double *zre, *zim;  // z_j per system
+};
+// q = z Sigma p - M p for every system (from the sigma and metric products of p)
+__global__ void k_rz_apply(double *__restrict__ q, const double *__restrict__ MP, const double *__restrict__ SP,
+                           const double *__restrict__ zre, const double *__restrict__ zim, long long L, int ns) {
+  const long long total = (long long)ns * L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(p / L);
+    const long long e = p % L, re = 2LL * s * L + e, im = re + L;
+    const double a = zre[s], b = zim[s];
+    const double sr = SP[re], si = SP[im];
+    q[re] = a * sr - b * si - MP[re];
+    q[im] = a * si + b * sr - MP[im];
+  }
+}
+// z = r / D, D = z_j diag(Sigma) - diag(M), diag(Sigma) = [dS; -dS], diag(M) = [dA; dA]
+__global__ void k_rz_prec(double *__restrict__ z, const double *__restrict__ r, const double *__restrict__ dA,
+                          const double *__restrict__ dS, const double *__restrict__ zre,
+                          const double *__restrict__ zim, long long ov, int ns) {
+  const long long L = 2 * ov, total = (long long)ns * L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(p / L);
+    const long long e = p % L, ia = e % ov, re = 2LL * s * L + e, im = re + L;
+    const double sg = (e < ov) ? dS[ia] : -dS[ia];
+    const double dr = zre[s] * sg - dA[ia], di = zim[s] * sg;
+    const double den = dr * dr + di * di;
+    const double xr = r[re], xi = r[im];
+    z[re] = (xr * dr + xi * di) / den;
+    z[im] = (xi * dr - xr * di) / den;
+  }
+}
+// per system: out[3 s] = Re(a^T b), out[3 s + 1] = Im(a^T b) (no conjugation), out[3 s + 2] = |a|^2
+__global__ void __launch_bounds__(256) k_rz_dot(const double *__restrict__ a, const double *__restrict__ b,
+                                                long long L, double *__restrict__ out) {
+  __shared__ double red[256];
+  const long long re = 2LL * blockIdx.x * L, im = re + L;
+  double sr = 0.0, si = 0.0, nn = 0.0;
+  for (long long e = threadIdx.x; e < L; e += blockDim.x) {
+    const double ar = a[re + e], ai = a[im + e], br = b[re + e], bi = b[im + e];
+    sr += ar * br - ai * bi;
+    si += ar * bi + ai * br;
+    nn += ar * ar + ai * ai;
+  }
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  nn = block_sum(nn, red);
+  if (threadIdx.x == 0) {
+    out[3 * blockIdx.x] = sr;
+    out[3 * blockIdx.x + 1] = si;
+    out[3 * blockIdx.x + 2] = nn;
+  }
+}
+// y += c x (complex c per system; c = (cf[2s], cf[2s+1])); mode 1: y = x + c y
+__global__ void k_rz_axpy(double *__restrict__ y, const double *__restrict__ x, const double *__restrict__ cf,
+                          long long L, int ns, int mode) {
+  const long long total = (long long)ns * L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(p / L);
+    const long long e = p % L, re = 2LL * s * L + e, im = re + L;
+    const double cr = cf[2 * s], ci = cf[2 * s + 1];
+    if (mode == 0) {
+      const double xr = x[re], xi = x[im];
+      y[re] += cr * xr - ci * xi;
+      y[im] += cr * xi + ci * xr;
+    } else {
+      const double yr = y[re], yi = y[im];
+      y[re] = x[re] + cr * yr - ci * yi;
+      y[im] = x[im] + cr * yi + ci * yr;
+    }
+  }
+}
+// right-hand sides: b_s = Sigma y_q (real), s = j m0 + q
+__global__ void k_rz_rhs(double *__restrict__ bvec, const double *__restrict__ SY, long long L, int m0, int ns) {
+  const long long total = (long long)ns * L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(p / L);
+    const long long e = p % L;
+    bvec[2LL * s * L + e] = SY[(long long)(s % m0) * L + e];
+    bvec[2LL * s * L + L + e] = 0.0;
+  }
+}
+// Q_q = sum_j Re(w_j X_{j m0 + q}), w_j = rho e^{i theta_j} / Nq
+__global__ void k_rz_accum(double *__restrict__ Qv, const double *__restrict__ X, const double *__restrict__ wre,
+                           const double *__restrict__ wim, long long L, int m0, int nq) {
+  const long long total = (long long)m0 * L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(p / L);
+    const long long e = p % L;
+    double acc = 0.0;
+    for (int j = 0; j < nq; ++j) {
+      const long long re = 2LL * (j * m0 + q) * L + e;
+      acc += wre[j] * X[re] - wim[j] * X[re + L];
+    }
+    Qv[p] = acc;
+  }
+}
+
+inline unsigned rz_blocks(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+}
+
+}  // namespace
+
+pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0_req, int max_outer, double *omega_out,
+                     double *osc_out, double *resid_out, int cap, int *nfound) {
+  cudaStream_t s = c->stream;
+  const long long ov = c->ov, L = 2 * ov;
+  const double ctr = omega0 + 0.5 * delta, rad = 0.5 * delta;
+  const bool mixed = c->opt.prec != PP_FP64;
+  const int p_filter = mixed ? PP_BF16 : PP_FP64, p_acc = mixed ? PP_BF16X3 : PP_FP64;
+  // subspace size: 1.5 x the diagonal estimate of the roots in the window, plus a margin
+  std::vector<double> hA(ov), hS(ov);
+  PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaMemcpyAsync(hS.data(), c->diagS.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
+  PP_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> ratio(ov);
+  int n_in = 0;
+  for (long long p = 0; p < ov; ++p) {
+    ratio[p] = hA[p] / hS[p];
+    if (ratio[p] >= omega0 && ratio[p] <= omega0 + delta) ++n_in;
+  }
+  int m0 = m0_req > 0 ? m0_req : std::max(8, (3 * n_in + 1) / 2 + 4);
+  m0 = std::min<int>(m0, (int)L);
+  if (m0 > 64)
+    throw PPError(PP_EINVAL, "pp_solve_window_contour: the window holds about " + std::to_string(n_in) +
+                                 " roots; the contour solver's subspace is limited to 64 vectors (narrow the window)");
+  const int nq = nquad;
+  const int ns = nq * m0;
+  // device memory: Y, MY, SY, Q, MQ, SQ (m0 each); complex x, r, z, p, q (2 ns each); sigma
+  // outputs of the complex batch (2 ns each, M and Sigma); small matrices
+  DevBuf mem;
+  const size_t vec = sizeof(double) * (size_t)L;
+  const size_t ndots = std::max<size_t>(3 * (size_t)ns, 8 * (size_t)MAXM);
+  const size_t small = sizeof(double) * (9 * (size_t)MAXM * MAXM + 4 * (size_t)MAXM + 4 * (size_t)ns + ndots +
+                                         2 * (size_t)nq + 128);
+  mem.ensure(vec * (6 * (size_t)m0 + 14 * (size_t)ns) + small);
+  double *Y = mem.as<double>(), *MY = Y + m0 * L, *SY = MY + m0 * L, *Qb = SY + m0 * L, *MQ = Qb + m0 * L,
+         *SQ = MQ + m0 * L;
+  double *X = SQ + m0 * L, *R = X + 2LL * ns * L, *Z = R + 2LL * ns * L, *P = Z + 2LL * ns * L,
+         *Qc = P + 2LL * ns * L, *MP = Qc + 2LL * ns * L, *SP = MP + 2LL * ns * L;
+  double *sm = SP + 2LL * ns * L;
+  double *G = sm, *T = G + MAXM * MAXM, *Lm = T + MAXM * MAXM, *Cw = Lm + MAXM * MAXM, *Yw = Cw + MAXM * MAXM,
+         *mu = Yw + MAXM * MAXM, *W = mu + MAXM, *Esel = W + MAXM * MAXM, *thsel = Esel + MAXM * MAXM,
+         *dinv = thsel + MAXM, *Ew = dinv + MAXM;
+  double *zre = Ew + MAXM * MAXM, *zim = zre + ns, *cf = zim + ns, *dots = cf + 2 * ns, *wre = dots + ndots,
+         *wim = wre + nq;
+  int *istat = reinterpret_cast<int *>(wim + nq);
+  int *kept = istat + 8;
+  Solver sv{c, s, L};
+  DevBuf part;
+  sv.part_elems = (size_t)296 * MAXM * MAXM;
+  part.ensure(sizeof(double) * sv.part_elems);
+  sv.part = part.as<double>();
+  sv.f64 = true;
+  // quadrature points and weights
+  std::vector<double> hzr(ns), hzi(ns), hwr(nq), hwi(nq);
+  for (int j = 0; j < nq; ++j) {
+    const double th = 3.14159265358979323846 * (j + 0.5) / nq;
+    hwr[j] = rad * std::cos(th) / nq;
+    hwi[j] = rad * std::sin(th) / nq;
+    for (int q = 0; q < m0; ++q) {
+      hzr[j * m0 + q] = ctr + rad * std::cos(th);
+      hzi[j * m0 + q] = rad * std::sin(th);
+    }
+  }
+  PP_CUDA(cudaMemcpyAsync(zre, hzr.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA(cudaMemcpyAsync(zim, hzi.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA(cudaMemcpyAsync(wre, hwr.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+  PP_CUDA(cudaMemcpyAsync(wim, hwi.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+  // initial block: unit vectors on the diagonal entries nearest the window centre
+  {
+    std::vector<long long> ord(ov);
+    std::iota(ord.begin(), ord.end(), 0);
+    const long long nb = std::min<long long>(m0, ov);
+    std::partial_sort(ord.begin(), ord.begin() + nb, ord.end(), [&](long long a, long long b2) {
+      const double da = std::fabs(ratio[a] - ctr), db = std::fabs(ratio[b2] - ctr);
+      return da < db || (da == db && a < b2);
+    });
+    std::vector<int> hidx(m0);
+    for (int j = 0; j < m0; ++j) hidx[j] = (int)(j < nb ? ord[j] : ov + ord[j - nb]);
+    PP_CUDA(cudaMemcpyAsync(kept, hidx.data(), sizeof(int) * m0, cudaMemcpyHostToDevice, s));
+    k_unit_vectors<<<dim3(64, m0), 256, 0, s>>>(Y, L, kept, m0);
+    PP_LAUNCH_CHECK("k_unit_vectors");
+    PP_CUDA(cudaStreamSynchronize(s));
+  }
+  // inner tolerance: the outer residual settles near 2e-3 times it (CPU emulation); BF16 filters
+  // cannot go much below 1e-4 (their operator error is ~1e-5)
+  const double tol_in = mixed ? 1e-4 : 1e-6;
+  const int max_in = 300;  // inner iterations per filter application (tens suffice here)
+  std::vector<double> th_prev;
+  std::vector<double> h_th, h_res, h_xsx;
+  pp_status status = PP_ENOTCONV;
+  int m = m0;
+  std::vector<int> sel;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // ---- filter: solve (z_j Sigma - M) X_s = Sigma Y_q for all systems (COCG) -----------
+    apply_sigma(c, m, Y, MY, SY, p_filter);  // Sigma Y (the metric product is exact in either form)
+    k_rz_rhs<<<rz_blocks(ns * L), 256, 0, s>>>(R, SY, L, m0, ns);
+    PP_LAUNCH_CHECK("k_rz_rhs");
+    PP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * 2 * (size_t)ns * L, s));
+    k_rz_prec<<<rz_blocks(ns * L), 256, 0, s>>>(Z, R, c->diagA.as<double>(), c->diagS.as<double>(), zre, zim, ov, ns);
+    PP_LAUNCH_CHECK("k_rz_prec");
+    PP_CUDA(cudaMemcpyAsync(P, Z, sizeof(double) * 2 * (size_t)ns * L, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> hd(3 * ns), bn(ns), rho_r(ns), rho_i(ns);
+    auto dot_all = [&](const double *a, const double *b) {
+      k_rz_dot<<<ns, 256, 0, s>>>(a, b, L, dots);
+      PP_LAUNCH_CHECK("k_rz_dot");
+      PP_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 3 * ns, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+    };
+    dot_all(R, Z);
+    for (int t = 0; t < ns; ++t) {
+      rho_r[t] = hd[3 * t];
+      rho_i[t] = hd[3 * t + 1];
+      bn[t] = std::sqrt(hd[3 * t + 2]);
+    }
+    std::vector<char> done(ns, 0);
+    std::vector<double> hc(2 * ns);
+    for (int it = 0; it < max_in; ++it) {
+      apply_sigma(c, 2 * ns, P, MP, SP, p_filter);
+      k_rz_apply<<<rz_blocks(ns * L), 256, 0, s>>>(Qc, MP, SP, zre, zim, L, ns);
+      PP_LAUNCH_CHECK("k_rz_apply");
+      dot_all(P, Qc);  // sigma_t = p^T q
+      for (int t = 0; t < ns; ++t) {
+        const double dr = hd[3 * t], di = hd[3 * t + 1], den = dr * dr + di * di;
+        if (done[t] || den == 0.0) {
+          hc[2 * t] = hc[2 * t + 1] = 0.0;
+          continue;
+        }
+        hc[2 * t] = (rho_r[t] * dr + rho_i[t] * di) / den;  // alpha = rho / sigma
+        hc[2 * t + 1] = (rho_i[t] * dr - rho_r[t] * di) / den;
+      }
+      PP_CUDA(cudaMemcpyAsync(cf, hc.data(), sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, s));
+      k_rz_axpy<<<rz_blocks(ns * L), 256, 0, s>>>(X, P, cf, L, ns, 0);  // x += alpha p
+      PP_LAUNCH_CHECK("k_rz_axpy");
+      for (int t = 0; t < 2 * ns; ++t) hc[t] = -hc[t];
+      PP_CUDA(cudaMemcpyAsync(cf, hc.data(), sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, s));
+      k_rz_axpy<<<rz_blocks(ns * L), 256, 0, s>>>(R, Qc, cf, L, ns, 0);  // r -= alpha q
+      PP_LAUNCH_CHECK("k_rz_axpy");
+      k_rz_prec<<<rz_blocks(ns * L), 256, 0, s>>>(Z, R, c->diagA.as<double>(), c->diagS.as<double>(), zre, zim, ov,
+                                                  ns);
+      PP_LAUNCH_CHECK("k_rz_prec");
+      dot_all(R, Z);
+      bool all = true;
+      for (int t = 0; t < ns; ++t) {
+        if (!done[t] && std::sqrt(hd[3 * t + 2]) > 0.0) {
+          // |r| from the same reduction: |r|^2 is the third output of the (r, z) dot
+          const double rn = std::sqrt(hd[3 * t + 2]);
+          if (rn <= tol_in * bn[t]) done[t] = 1;
+        }
+        const double nr = hd[3 * t], ni = hd[3 * t + 1];
+        const double den = rho_r[t] * rho_r[t] + rho_i[t] * rho_i[t];
+        if (done[t] || den == 0.0) {
+          hc[2 * t] = hc[2 * t + 1] = 0.0;
+        } else {
+          hc[2 * t] = (nr * rho_r[t] + ni * rho_i[t]) / den;  // beta = rho' / rho
+          hc[2 * t + 1] = (ni * rho_r[t] - nr * rho_i[t]) / den;
+        }
+        rho_r[t] = nr;
+        rho_i[t] = ni;
+        all = all && done[t];
+      }
+      if (all) break;
+      PP_CUDA(cudaMemcpyAsync(cf, hc.data(), sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, s));
+      k_rz_axpy<<<rz_blocks(ns * L), 256, 0, s>>>(P, Z, cf, L, ns, 1);  // p = z + beta p
+      PP_LAUNCH_CHECK("k_rz_axpy");
+    }
+    k_rz_accum<<<rz_blocks(m0 * L), 256, 0, s>>>(Qb, X, wre, wim, L, m0, nq);
+    PP_LAUNCH_CHECK("k_rz_accum");
+    // ---- orthonormalise the filtered block (Cholesky QR twice), then its products ----------
+    int nk = m0;
+    for (int pass = 0; pass < 2 && nk > 0; ++pass) {
+      sv.gram(Qb, L, nk, Qb, L, nk, G, nk);
+      k_cholqr<<<1, 32, 0, s>>>(G, nk, pass == 0 ? 1e-14 : 1e-10, T, kept);
+      PP_LAUNCH_CHECK("k_cholqr");
+      std::vector<int> hk(nk);
+      PP_CUDA(cudaMemcpyAsync(hk.data(), kept, sizeof(int) * nk, cudaMemcpyDeviceToHost, s));
+      PP_CUDA(cudaStreamSynchronize(s));
+      sv.combine(Qb, nk, T, nk, nk, Y, 1.0, 0.0);  // staged in Y
+      int w2 = 0;
+      for (int j = 0; j < nk; ++j) {
+        if (!hk[j]) continue;
+        PP_CUDA(cudaMemcpyAsync(Qb + (long long)w2 * L, Y + (long long)j * L, vec, cudaMemcpyDeviceToDevice, s));
+        ++w2;
+      }
+      nk = w2;
+    }
+    if (nk == 0) throw PPError(PP_ECUDA, "pp_solve_window_contour: the filtered block vanished");
+    m = nk;
+    apply_sigma(c, m, Qb, MQ, SQ, p_acc);
+    // ---- Rayleigh-Ritz on (Q^T M Q, Q^T Sigma Q): all m pairs, nearest the centre first ------
+    sv.gram(Qb, L, m, MQ, L, m, G, m);      // Hm
+    sv.gram(Qb, L, m, SQ, L, m, T, m);      // Hs
+    PP_CUDA(cudaMemsetAsync(istat, 0, sizeof(int) * 4, s));
+    k_chol_rr<<<1, 256, (m * (m + 1) + 2 * m) * sizeof(double), s>>>(G, m, Lm, dinv, istat);
+    PP_LAUNCH_CHECK("k_chol_rr");
+    k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(T, Lm, dinv, m, 0, Yw, istat);
+    PP_LAUNCH_CHECK("k_rr_trsm");
+    k_rr_trsm<<<(m + 3) / 4, 128, 0, s>>>(Yw, Lm, dinv, m, 1, Cw, istat);
+    PP_LAUNCH_CHECK("k_rr_trsm");
+    const int mp = (m + 1) & ~1;
+    k_jacobi_eig_f64<<<1, 512, 2 * mp * mp * sizeof(double), s>>>(Cw, m, mu, W, 16);
+    PP_LAUNCH_CHECK("k_jacobi_eig");
+    k_rr_select<<<1, 128, 0, s>>>(Lm, mu, W, m, ctr, m, Ew, thsel, Esel);
+    PP_LAUNCH_CHECK("k_rr_select");
+    // Ritz vectors (unit norm) and their products, in Y / MY / SY (the next block to filter)
+    sv.combine(Qb, m, Esel, m, m, Y, 1.0, 0.0);
+    sv.combine(MQ, m, Esel, m, m, MY, 1.0, 0.0);
+    sv.combine(SQ, m, Esel, m, m, SY, 1.0, 0.0);
+    k_ritz_dots<<<m, 256, 0, s>>>(Y, MY, SY, L, dots);
+    PP_LAUNCH_CHECK("k_ritz_dots");
+    std::vector<double> rd(3 * m);
+    int hstat = 0;
+    PP_CUDA(cudaMemcpyAsync(rd.data(), dots, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaMemcpyAsync(&hstat, istat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    if (hstat) throw PPError(PP_EUNSTABLE, "projected M is not positive definite (unstable RPA problem)");
+    h_th.assign(m, 0.0);
+    h_xsx.assign(m, 0.0);
+    for (int j = 0; j < m; ++j) {
+      h_xsx[j] = rd[3 * j + 1] / rd[3 * j + 2];
+      h_th[j] = rd[3 * j] / rd[3 * j + 1];
+    }
+    double *theta_d = dots + 3 * MAXM, *rn = theta_d + MAXM;
+    PP_CUDA(cudaMemcpyAsync(theta_d, h_th.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    // residual norms (the direction output lands in the complex work buffer, unused)
+    k_resid_dir<<<m, 256, 0, s>>>(Y, MY, SY, theta_d, c->diagA.as<double>(), c->diagS.as<double>(), ov,
+                                  c->opt.jacobi_floor, X, rn);
+    PP_LAUNCH_CHECK("k_resid_dir");
+    std::vector<double> hr(m);
+    PP_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    PP_CUDA(cudaStreamSynchronize(s));
+    h_res.assign(m, 0.0);
+    for (int j = 0; j < m; ++j) h_res[j] = std::sqrt(hr[j] / rd[3 * j + 2]) / std::fabs(h_xsx[j]);
+    sel.clear();
+    for (int j = 0; j < m; ++j)
+      if (h_th[j] >= omega0 && h_th[j] <= omega0 + delta) sel.push_back(j);
+    bool conv = true;
+    for (int j : sel) conv = conv && h_res[j] <= c->opt.res_tol;
+    std::vector<double> th_now;
+    for (int j : sel) th_now.push_back(h_th[j]);
+    std::sort(th_now.begin(), th_now.end());
+    if (const char *e = std::getenv("PP_LOG"); e && e[0] && e[0] != '0') {
+      double worst = 0.0;
+      for (int j : sel) worst = std::max(worst, h_res[j]);
+      std::fprintf(stderr, "[pp] contour it %d m %d in-window %zu worst %.2e\n", outer, m, sel.size(), worst);
+    }
+    // converged: every Ritz value in the window meets the tolerance and the count is stable
+    if (conv && th_now.size() == th_prev.size()) {
+      status = PP_OK;
+      break;
+    }
+    th_prev = th_now;
+    if (m < m0) {  // refill the block to m0 with unit vectors (the filter needs m0 >= roots inside)
+      PP_CUDA(cudaMemsetAsync(Y + (long long)m * L, 0, vec * (m0 - m), s));
+    }
+    m = m0;
+  }
+  // results: the Ritz pairs inside the window, ascending
+  std::sort(sel.begin(), sel.end(), [&](int a, int b2) { return h_th[a] < h_th[b2]; });
+  const int nf = (int)sel.size();
+  *nfound = nf;
+  if (nf > cap) {
+    c->err = "pp_solve_window_contour: " + std::to_string(nf) + " roots in the window exceed k = " + std::to_string(cap);
+    return PP_EINVAL;
+  }
+  if (nf > 0) {
+    double *thd = dots, *xsd = dots + MAXM, *od = dots + 2 * MAXM;
+    std::vector<double> th(nf), xs(nf);
+    for (int t = 0; t < nf; ++t) {
+      th[t] = h_th[sel[t]];
+      xs[t] = h_xsx[sel[t]];
+      PP_CUDA(cudaMemcpyAsync(Qb + (long long)t * L, Y + (long long)sel[t] * L, vec, cudaMemcpyDeviceToDevice, s));
+    }
+    PP_CUDA(cudaMemcpyAsync(thd, th.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+    PP_CUDA(cudaMemcpyAsync(xsd, xs.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+    std::vector<double> ho(nf, 0.0);
+    if (c->has_mu) {
+      k_osc<<<nf, 256, 0, s>>>(Qb, c->mu.as<double>(), ov, thd, xsd, od);
+      PP_LAUNCH_CHECK("k_osc");
+      PP_CUDA(cudaMemcpyAsync(ho.data(), od, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+    }
+    PP_CUDA(cudaStreamSynchronize(s));
+    for (int t = 0; t < nf; ++t) {
+      omega_out[t] = th[t];
+      osc_out[t] = ho[t];
+      resid_out[t] = h_res[sel[t]];
+    }
+  }
+  return status;
+}

@@ -1256,7 +1256,7 @@ struct TcPlan {
   DevBuf bvvK_hi, bvvK_lo;   // [a][(Q,b)]         KA = sum_(Q,b) U_Q Bvv_Q
   DevBuf gbT_hi, gbT_lo;     // [a][(t,j)]         KB = sum_t EF_t GB_t
   // FP32 copies of the operands of the remaining SIMT contractions
-  DevBuf f_gap, f_eps, f_Bov, f_Boo, f_Bvv, f_BvvP, f_BooT, f_GB, f_Gam, f_poo, f_qoo, f_pvv, f_qvv;
+  DevBuf f_eps, f_Bov, f_poo, f_qoo, f_pvv, f_qvv;
   // workspaces
   DevBuf w_V, w_acc, w_tmp, w_cq, w_W, w_U, w_EF;
   DevBuf v_hi, v_lo;         // [(r,j)][vp]
@@ -1274,8 +1274,8 @@ size_t tc_plan_bytes(const pp_ctx *c) {
   if (!c->tc) return 0;
   TcPlan *p = c->tc;
   const DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->bvv_hi, &p->bvv_lo, &p->bov_hi, &p->bov_lo, &p->gam_hi,
-                          &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_gap, &p->f_eps,
-                          &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
+                          &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_eps,
+                          &p->f_Bov, &p->f_poo,
                           &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                           &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                           &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
@@ -1290,8 +1290,8 @@ void tc_destroy(pp_ctx *c) {
   if (!c->tc) return;
   TcPlan *p = c->tc;
   DevBuf *bufs[] = {&p->bovT_hi, &p->bovT_lo, &p->bvv_hi, &p->bvv_lo, &p->bov_hi, &p->bov_lo, &p->gam_hi,
-                    &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_gap, &p->f_eps,
-                    &p->f_Bov, &p->f_Boo, &p->f_Bvv, &p->f_BvvP, &p->f_BooT, &p->f_GB, &p->f_Gam, &p->f_poo,
+                    &p->gam_lo, &p->bvvT_hi, &p->bvvT_lo, &p->booT_hi, &p->booT_lo, &p->f_eps,
+                    &p->f_Bov, &p->f_poo,
                     &p->f_qoo, &p->f_pvv, &p->f_qvv, &p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->w_W,
                     &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                     &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
@@ -1368,13 +1368,11 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   p->ldT = pad64(ov);
   p->vp = pad64(v);
   p->Qp = pad64(Q);
-  f32_copy(p->f_gap, c->gap, ov, s);
+  // FP32 copies of the operands of the SIMT contractions that remain in this form (the
+  // Coulomb term and the A(2) pair-sum products); the exchange and amplitude contractions
+  // read only their BF16 pairs, so no FP32 copy of Boo, Bvv, Gamma or GB is kept
   f32_copy(p->f_eps, c->eps, c->n, s);
   f32_copy(p->f_Bov, c->Bov, Q * ov, s);
-  f32_copy(p->f_Boo, c->Boo, Q * o * o, s);
-  f32_copy(p->f_Bvv, c->Bvv, Q * v * v, s);
-  f32_copy(p->f_BvvP, c->BvvP, Q * v * v, s);
-  f32_copy(p->f_BooT, c->BooT, Q * o * o, s);
   p->kbo = pad64(o);
   p->kqv = pad64(Q * v);
   p->kef = pad64(2 * Q * o);
@@ -1409,8 +1407,11 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
     PP_LAUNCH_CHECK("k_perm_qlast");
   }
   // chunk of R half-vectors: FP32 W, U, E/F plus BF16 C_Q(V) and two BF16 copies of P
-  const long long per_half = 4 * (2 * Q * ov + 2 * Q * o * o + 8 * ov + Q) + 2 * 2 * Q * p->ldT +
-                             2 * 2 * 2 * ov * p->Qp + 2 * 2 * o * p->kqv;
+  // bytes per half-vector of the chunk workspaces sigma_bf16 allocates: FP32 V, accumulators and
+  // temporaries (7 ov) and c_Q; BF16 pairs (4 bytes per element) of V, V^T, U, E/F, C_Q(V) and
+  // the two layouts of P
+  const long long per_half = 4 * (7 * ov + Q) + 4 * (o * p->vp + v * p->kbo + o * p->kqv + o * p->kef) +
+                             4 * Q * p->ldT + 8 * ov * p->Qp;
   long long R = tc_workspace_bytes(c) / std::max<long long>(per_half, 1);
   R = std::max<long long>(2, std::min<long long>(R, 64));
   R &= ~1LL;
@@ -1433,8 +1434,6 @@ static TcPlan *tc_plan(pp_ctx *c) {
   if (p->ready) return p;
   const long long o = c->o, v = c->v, Q = c->Q, ov = c->ov;
   cudaStream_t s = c->stream;
-  f32_copy(p->f_GB, c->GB, 2 * Q * ov, s);
-  f32_copy(p->f_Gam, c->Gam, Q * ov, s);
   f32_copy(p->f_poo, c->p_oo, o * o, s);
   f32_copy(p->f_qoo, c->q_oo, o * o, s);
   f32_copy(p->f_pvv, c->p_vv, v * v, s);
@@ -1613,10 +1612,10 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     ensure_zeroed(p->p2_hi, pbytes, s);
     ensure_zeroed(p->p2_lo, pbytes, s);
   }
-  SigmaRes<float> res{p->f_gap.as<float>(), p->f_eps.as<float>(), p->f_Bov.as<float>(), p->f_Boo.as<float>(),
-                      p->f_Bvv.as<float>(), p->f_BvvP.as<float>(), p->f_BooT.as<float>(), p->f_GB.as<float>(),
-                      p->f_Gam.as<float>(), p->f_poo.as<float>(), p->f_qoo.as<float>(), p->f_pvv.as<float>(),
-                      p->f_qvv.as<float>()};
+  // gap, Boo, Bvv, BvvP, BooT, GB and Gamma in FP32 are only read by the step-by-step fallback of
+  // sigma_chunk, which the first_order hook below replaces (it always returns true)
+  SigmaRes<float> res{nullptr, p->f_eps.as<float>(), p->f_Bov.as<float>(), nullptr, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, p->f_poo.as<float>(), p->f_qoo.as<float>(), p->f_pvv.as<float>(), p->f_qvv.as<float>()};
   int *err = p->err.as<int>();
   const bf *vhi = p->v_hi.as<bf>(), *vlo = p->v_lo.as<bf>();
   auto seg3 = [&](const bf *hiA, const bf *loA, const bf *hiB, const bf *loB, const bf **A, const bf **B) {
