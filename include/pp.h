@@ -91,6 +91,8 @@ typedef struct {
   int tda;             /* 1: Tamm-Dancoff form (Sec. 2.2 with B = 0): M = diag(A, A), so the
                           roots are those of A X = omega S X and the sigma products skip every
                           B term (the amplitude contraction included); 0 (default): full form */
+  int graphs;          /* tensor-core sigma: 1 (default) replays each chunk shape met before as a
+                          captured CUDA graph; 0 launches kernel by kernel */
 } pp_options;
 
 /* Fill *opt with the defaults above. */

@@ -40,7 +40,7 @@ class pp_options(C.Structure):
         ("prec", C.c_int), ("order", C.c_int), ("block", C.c_int), ("m_max", C.c_int),
         ("max_iter", C.c_int), ("res_tol", C.c_double), ("jacobi_floor", C.c_double),
         ("select", C.c_int), ("refine", C.c_int), ("seed", C.c_uint64), ("cuda_stream", C.c_void_p),
-        ("workspace_gb", C.c_double), ("tda", C.c_int),
+        ("workspace_gb", C.c_double), ("tda", C.c_int), ("graphs", C.c_int),
     ]
 
 

@@ -30,6 +30,7 @@ extern "C" void pp_default_options(pp_options *opt) {
   opt->refine = 1;
   opt->seed = 0;
   opt->cuda_stream = nullptr;
+  opt->graphs = 1;
 }
 
 static bool all_finite(const double *x, size_t n) {
@@ -96,7 +97,7 @@ extern "C" pp_status pp_create(int nocc, int nvir, int naux, const double *eps, 
   else pp_default_options(&o);
   if (o.order < 0 || o.order > 2 || (o.prec != PP_FP64 && o.prec != PP_BF16 && o.prec != PP_BF16X3) || o.block < 1 ||
       o.m_max < 4 || !(o.res_tol > 0) || !(o.jacobi_floor > 0) || (o.select != 0 && o.select != 1) ||
-      !(o.workspace_gb >= 0) || o.workspace_gb > 1e5 || (o.tda != 0 && o.tda != 1)) {
+      !(o.workspace_gb >= 0) || o.workspace_gb > 1e5 || (o.tda != 0 && o.tda != 1) || (o.graphs != 0 && o.graphs != 1)) {
     g_create_err = "pp_create: bad options";
     return PP_EINVAL;
   }

@@ -27,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -980,6 +981,12 @@ static void launch_gemm_t(const GemmMaps &m, const GemmArgs &a, dim3 grid, cudaS
   k_gemm_bf16<BN, ST><<<grid, 128, gemm_smem_cfg(BN, ST), s>>>(m, a);
   PP_LAUNCH_CHECK("k_gemm_bf16");
 }
+// shared-memory limits of every tile configuration and of the generators, set once before any
+// capture of a stream (a stream being captured must see only kernel launches and copies)
+template <int BN, int ST> static void gemm_attr_t() {
+  PP_CUDA(cudaFuncSetAttribute(k_gemm_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gemm_smem_cfg(BN, ST)));
+}
 static void launch_gemm_cfg(int cfg, const GemmMaps &m, const GemmArgs &a, dim3 grid, cudaStream_t s) {
   switch (cfg) {
     case 0: launch_gemm_t<256, 4>(m, a, grid, s); break;
@@ -1012,6 +1019,8 @@ struct TuneVal {
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
+static thread_local bool g_tune_blocked = false;  // inside a stream capture: no timing runs
+void tune_block(bool on) { g_tune_blocked = on; }
 static long long g_tune_runs = 0;  // tunings performed in this process
 static bool g_tune_init = false, g_tune_on = true;
 static std::string g_tune_file;
@@ -1102,7 +1111,7 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
       chosen = it->second;
       have = true;
     } else {
-      tune = g_tune_on && (!acc || (acc_base && acc_bytes));
+      tune = g_tune_on && !g_tune_blocked && (!acc || (acc_base && acc_bytes));
     }
   }
   if (have) {
@@ -1187,6 +1196,18 @@ void tgen(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq
   PP_LAUNCH_CHECK("k_tgen");
 }
 
+void prepare_kernels() {
+  static bool done = false;
+  if (done) return;
+  gemm_attr_t<256, 4>();
+  gemm_attr_t<256, 2>();
+  gemm_attr_t<128, 6>();
+  gemm_attr_t<128, 3>();
+  PP_CUDA(cudaFuncSetAttribute(k_tgen_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tgenp_smem()));
+  PP_CUDA(cudaFuncSetAttribute(k_tgen<TGEN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tgen_smem()));
+  done = true;
+}
+
 // persistent amplitude slab (sigma product): one CTA per SM over the (i, j, ct <= dt) items
 void tgen_p(const __nv_bfloat16 *bovT, const __nv_bfloat16 *bovT_lo, long long ldq, long long ov, int o, int v,
             int i0, int ni, const float *eps, __nv_bfloat16 *Thi, __nv_bfloat16 *Tlo, long long ldT, int *err,
@@ -1238,6 +1259,10 @@ struct KernelProfile {
   double flops[NPROF] = {0, 0, 0};
   double ms[NPROF] = {0, 0, 0};
 };
+struct ChunkGraph {
+  cudaGraphExec_t exec;
+  long long kernels;  // kernel nodes of the graph (launch accounting)
+};
 struct TcPlan {
   long long ldq = 0, ldT = 0, vp = 0, Qp = 0;
   bool ready = false;  // copies of the per-dot intermediates made (after the precompute)
@@ -1268,6 +1293,11 @@ struct TcPlan {
   DevBuf kaU_hi, kaU_lo;     // U as [(r,i)][(Q,b)]
   DevBuf efB_hi, efB_lo;     // E, F as [(r,i)][(t,j)]
   DevBuf err;
+  // CUDA graphs of sigma chunks (key: R, form, metric) and their staging buffers
+  std::map<long long, ChunkGraph> graph_exec;
+  std::set<long long> graph_seen;
+  size_t graph_sig = 0;
+  DevBuf g_in, g_sig, g_met;
 };
 
 size_t tc_plan_bytes(const pp_ctx *c) {
@@ -1280,10 +1310,25 @@ size_t tc_plan_bytes(const pp_ctx *c) {
                           &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                           &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
                           &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo,
-                          &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
+                          &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo, &p->g_in, &p->g_sig, &p->g_met};
   size_t n = 0;
   for (const DevBuf *b : bufs) n += b->bytes;
   return n;
+}
+
+static void clear_chunk_graphs(TcPlan *p) {
+  for (auto &kv : p->graph_exec) cudaGraphExecDestroy(kv.second.exec);
+  p->graph_exec.clear();
+  p->graph_seen.clear();
+}
+// the addresses a captured chunk reads and writes (a change means the workspaces moved)
+static size_t chunk_buffers_signature(const TcPlan *p) {
+  const DevBuf *bufs[] = {&p->w_V, &p->w_acc, &p->w_tmp, &p->w_cq, &p->v_hi, &p->v_lo, &p->kaU_hi, &p->kaU_lo,
+                          &p->vT_hi, &p->vT_lo, &p->efB_hi, &p->efB_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
+                          &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->g_in, &p->g_sig, &p->g_met};
+  size_t h = 1469598103934665603ull;
+  for (const DevBuf *b : bufs) h = (h ^ reinterpret_cast<uintptr_t>(b->p)) * 1099511628211ull;
+  return h;
 }
 
 void tc_destroy(pp_ctx *c) {
@@ -1296,8 +1341,9 @@ void tc_destroy(pp_ctx *c) {
                     &p->w_U, &p->w_EF, &p->v_hi, &p->v_lo, &p->c_hi, &p->c_lo, &p->t_hi, &p->t_lo,
                     &p->p1_hi, &p->p1_lo, &p->p2_hi, &p->p2_lo, &p->err, &p->booK_hi, &p->booK_lo,
                     &p->bvvK_hi, &p->bvvK_lo, &p->gbT_hi, &p->gbT_lo, &p->vT_hi, &p->vT_lo,
-                    &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo};
+                    &p->kaU_hi, &p->kaU_lo, &p->efB_hi, &p->efB_lo, &p->g_in, &p->g_sig, &p->g_met};
   for (DevBuf *b : bufs) b->release();
+  clear_chunk_graphs(p);
   for (auto &v : p->prof.ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   delete p;
@@ -1580,6 +1626,7 @@ static void ensure_zeroed(DevBuf &b, size_t bytes, cudaStream_t s) {
 // (three products) for an FP32-level result.
 void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split) {
   TcPlan *p = tc_plan(c);
+  tc::prepare_kernels();
   const int o = c->o, v = c->v, Q = c->Q;
   const long long ov = c->ov, vp = p->vp, Qp = p->Qp, ldT = p->ldT;
   cudaStream_t s = c->stream;
@@ -1624,9 +1671,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     A[2] = loA; B[2] = hiB;
   };
   const int R_total = 2 * nvec;
-  for (int r0 = 0; r0 < R_total; r0 += Rmax) {
-    const int R = std::min(Rmax, R_total - r0);
-    const double *V64 = Zd + (long long)r0 * ov;
+  // one chunk of R half-vectors: V64 in, sg_out / mt_out (mt_out may be null) out
+  auto run_chunk = [&](const int R, const double *V64, double *sg_out, double *mt_out) {
     float *V = p->w_V.as<float>();
     tc::k_d2f<<<tc::grid_for((long long)R * ov), 256, 0, s>>>(V64, V, (long long)R * ov);
     PP_LAUNCH_CHECK("k_d2f");
@@ -1821,8 +1867,71 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
                       (long long)o * Qp, out, err, s, nullptr, Bacc, sizeof(float) * (size_t)Rc * ov);
       }
     };
-    sigma_chunk<float>(c, R, V, V64, sig_d + (long long)r0 * ov, met_d ? met_d + (long long)r0 * ov : nullptr,
-                       res, wk, hk);
+    sigma_chunk<float>(c, R, V, V64, sg_out, mt_out, res, wk, hk);
+  };
+  // A chunk shape (R, form, metric or not) met for the second time is captured into a CUDA
+  // graph that reads and writes fixed staging buffers; later chunks of that shape copy their
+  // half-vectors in, replay the graph and copy the products out.  The first run of a shape
+  // goes kernel by kernel (the GEMM autotuner settles its choices there: a capture cannot
+  // time anything, so inside one the tuner uses its table or the default rule).  Not while
+  // the profiling events are recorded.
+  const bool graphs = c->opt.graphs != 0 && !p->prof.on;
+  if (graphs) {
+    const size_t sig = chunk_buffers_signature(p);
+    if (sig != p->graph_sig) {  // workspaces reallocated since the graphs were captured
+      clear_chunk_graphs(p);
+      p->graph_sig = sig;
+    }
+    p->g_in.ensure(sizeof(double) * (size_t)Rmax * ov);
+    p->g_sig.ensure(sizeof(double) * (size_t)Rmax * ov);
+    p->g_met.ensure(sizeof(double) * (size_t)Rmax * ov);
+  }
+  for (int r0 = 0; r0 < R_total; r0 += Rmax) {
+    const int R = std::min(Rmax, R_total - r0);
+    const double *V64 = Zd + (long long)r0 * ov;
+    double *sg = sig_d + (long long)r0 * ov, *mt = met_d ? met_d + (long long)r0 * ov : nullptr;
+    if (!graphs) {
+      run_chunk(R, V64, sg, mt);
+      continue;
+    }
+    const long long key = ((long long)R << 2) | (split ? 2 : 0) | (mt ? 1 : 0);
+    auto it = p->graph_exec.find(key);
+    const size_t bytes = sizeof(double) * (size_t)R * ov;
+    if (it == p->graph_exec.end() && !p->graph_seen.count(key)) {
+      p->graph_seen.insert(key);
+      run_chunk(R, V64, sg, mt);
+      continue;
+    }
+    double *gin = p->g_in.as<double>(), *gsg = p->g_sig.as<double>(), *gmt = mt ? p->g_met.as<double>() : nullptr;
+    PP_CUDA(cudaMemcpyAsync(gin, V64, bytes, cudaMemcpyDeviceToDevice, s));
+    if (it == p->graph_exec.end()) {
+      cudaGraph_t g = nullptr;
+      const unsigned long long launches0 = __atomic_load_n(&g_pp_launches, __ATOMIC_RELAXED);
+      PP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      tc::tune_block(true);
+      try {
+        run_chunk(R, gin, gsg, gmt);
+      } catch (...) {
+        tc::tune_block(false);
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      tc::tune_block(false);
+      PP_CUDA(cudaStreamEndCapture(s, &g));
+      cudaGraphExec_t ge = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) throw PPError(PP_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+      // the kernels of the capture were counted once while recording; count them per replay
+      const long long nk = (long long)(__atomic_load_n(&g_pp_launches, __ATOMIC_RELAXED) - launches0);
+      __atomic_fetch_sub(&g_pp_launches, (unsigned long long)nk, __ATOMIC_RELAXED);
+      it = p->graph_exec.emplace(key, ChunkGraph{ge, nk}).first;
+    }
+    PP_CUDA(cudaGraphLaunch(it->second.exec, s));
+    __atomic_fetch_add(&g_pp_launches, (unsigned long long)it->second.kernels, __ATOMIC_RELAXED);
+    PP_CUDA(cudaMemcpyAsync(sg, gsg, bytes, cudaMemcpyDeviceToDevice, s));
+    if (mt) PP_CUDA(cudaMemcpyAsync(mt, gmt, bytes, cudaMemcpyDeviceToDevice, s));
   }
   int herr = 0;
   PP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -65,3 +65,36 @@ def test_sigma_bf16_elementwise(cuda_lib, case, ctx_prec):
     finally:
         dot.close()
 
+
+
+def test_sigma_chunk_graphs_replay(cuda_lib):
+    """The tensor-core sigma replays each chunk shape it has met before as a captured CUDA
+    graph (first call kernel by kernel, second captured, third replayed): every call agrees
+    with the kernel-by-kernel context to FP32-reduction noise and stays within the bounds."""
+    pp = cuda_lib
+    o, v, Q = 16, 130, 70
+    inp = make_inputs(o, v, Q, seed=7, mode="scaled")
+    ref = po.SigmaRef(inp.eps, inp.B, o, order=2)
+    Z = random_vectors(3, o, v, seed=14)
+    want = ref.sigma(Z)
+    scale = sigma_scales(ref, Z)
+    plain = pp.Dot(inp, order=2, prec=pp.PP_BF16, graphs=0)
+    graph = pp.Dot(inp, order=2, prec=pp.PP_BF16, graphs=1)
+    try:
+        for name in ("PP_BF16", "PP_BF16X3"):
+            prec = getattr(pp, name)
+            base, base_m = plain.sigma(Z, prec=prec, metric=True)
+            for call in range(3):
+                got, met = graph.sigma(Z, prec=prec, metric=True)
+                assert np.abs(got - base).max() <= 1e-6 * np.abs(base).max(), (name, call)
+                # two contexts: their FP32 split-K pair sums differ in the last bits
+                assert np.abs(met - base_m).max() <= 1e-8 * np.abs(base_m).max()
+                r, at = elementwise_ok(got, want, scale, name)
+                assert r <= 1.0, (name, call, r, at)
+            # the same shape without the metric output is a different graph
+            for call in range(2):
+                got = graph.sigma(Z, prec=prec)
+                assert np.abs(got - base).max() <= 1e-6 * np.abs(base).max()
+    finally:
+        plain.close()
+        graph.close()
