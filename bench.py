@@ -530,15 +530,15 @@ def profile_workload(args):
 
     w = WORKLOADS[args.workload]
     inp = make_dot_inputs(w)
-    if args.profile_sigma:
-        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], workspace_gb=args.profile_workspace_gb)
+    if args.profile_sigma:  # kernel by kernel (no chunk graphs), for per-launch profiles
+        dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], workspace_gb=args.profile_workspace_gb, graphs=0)
         Z = torch.from_numpy(random_vectors(args.profile_sigma, w["nocc"], w["nvir"], seed=5)).cuda()
         for prec in (pp.PP_BF16, pp.PP_BF16X3):
             pp.pp_sigma(dot.ctx, Z, prec=prec)
         torch.cuda.synchronize()
     else:
         dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"],
-                     max_iter=args.profile_solve)
+                     max_iter=args.profile_solve, graphs=0)
         dA, dS = dot.diagonal()
         omega0 = float(np.percentile((dA / dS).ravel(), w["pct"]))
         dot.solve_windows(windows_for_rank(omega0, w["delta"], w["nwin"], 0), [w["delta"]] * w["nwin"],

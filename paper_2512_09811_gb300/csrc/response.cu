@@ -94,7 +94,8 @@ __global__ void k_lr_wx(double *__restrict__ wn, const double *__restrict__ v, c
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(p / L);
-    const double w = (v[p] - coef[c] * w1[p] - coef[NR + c] * w2[p]) * coef[2 * NR + c];
+    const double g = coef[2 * NR + c];
+    const double w = g != 0.0 ? (v[p] - coef[c] * w1[p] - coef[NR + c] * w2[p]) * g : 0.0;  // 0: frozen
     wn[p] = w;
     x[p] += coef[3 * NR + c] * w;
   }
@@ -163,16 +164,22 @@ struct Lr {
       cs[q] = -1.0;
       sn[q] = 0.0;
     }
+    // a right-hand side that has converged is frozen: all its coefficients are zero from then
+    // on (its Lanczos recurrence would otherwise run on with a vanishing beta)
+    bool conv[NR];
+    for (int q = 0; q < NR; ++q) conv[q] = !(beta1[q] > 0.0);
     double cf[4 * NR];
     int it = 0;
     for (; it < max_it; ++it) {
       bool done = true;
-      for (int q = 0; q < NR; ++q)
-        if (beta1[q] > 0.0 && phibar[q] > tol * beta1[q]) done = false;
+      for (int q = 0; q < NR; ++q) {
+        conv[q] = conv[q] || phibar[q] <= tol * beta1[q];
+        done = done && conv[q];
+      }
       if (done) break;
       // v = y / beta
       for (int q = 0; q < NR; ++q) {
-        cf[q] = beta[q] > 0.0 ? 1.0 / beta[q] : 0.0;
+        cf[q] = (!conv[q] && beta[q] > 0.0) ? 1.0 / beta[q] : 0.0;
         cf[NR + q] = 0.0;
       }
       set_coef(cf, 2 * NR);
@@ -182,7 +189,7 @@ struct Lr {
       apply(v, y, omega, prec_id);
       if (it > 0) {
         for (int q = 0; q < NR; ++q) {
-          cf[q] = oldb[q] != 0.0 ? -beta[q] / oldb[q] : 0.0;
+          cf[q] = (!conv[q] && oldb[q] != 0.0) ? -beta[q] / oldb[q] : 0.0;
           cf[NR + q] = 1.0;
         }
         set_coef(cf, 2 * NR);
@@ -193,7 +200,7 @@ struct Lr {
       dot(v, y, alfa);
       // y -= (alfa / beta) r2; then r1 <- r2, r2 <- y (pointer rotation), y = P^-1 r2
       for (int q = 0; q < NR; ++q) {
-        cf[q] = beta[q] > 0.0 ? -alfa[q] / beta[q] : 0.0;
+        cf[q] = (!conv[q] && beta[q] > 0.0) ? -alfa[q] / beta[q] : 0.0;
         cf[NR + q] = 1.0;
       }
       set_coef(cf, 2 * NR);
@@ -203,25 +210,28 @@ struct Lr {
       std::swap(r2, y);   // r2 <- new residual vector; y is free
       prec(y, r2, omega);
       dot(r2, y, h);
-      double delta[NR], gamma[NR], phi[NR], oldeps[NR];
       for (int q = 0; q < NR; ++q) {
+        if (conv[q]) {
+          cf[q] = cf[NR + q] = cf[2 * NR + q] = cf[3 * NR + q] = 0.0;
+          continue;
+        }
         oldb[q] = beta[q];
         beta[q] = std::sqrt(std::max(h[q], 0.0));
-        oldeps[q] = epsln[q];
-        delta[q] = cs[q] * dbar[q] + sn[q] * alfa[q];
+        const double oldeps = epsln[q];
+        const double delta = cs[q] * dbar[q] + sn[q] * alfa[q];
         const double gbar = sn[q] * dbar[q] - cs[q] * alfa[q];
         epsln[q] = sn[q] * beta[q];
         dbar[q] = -cs[q] * beta[q];
-        gamma[q] = std::sqrt(gbar * gbar + beta[q] * beta[q]);
-        if (gamma[q] == 0.0) gamma[q] = 1e-300;
-        cs[q] = gbar / gamma[q];
-        sn[q] = beta[q] / gamma[q];
-        phi[q] = cs[q] * phibar[q];
+        double gamma = std::sqrt(gbar * gbar + beta[q] * beta[q]);
+        if (!(gamma > 0.0)) gamma = 1e-300;
+        cs[q] = gbar / gamma;
+        sn[q] = beta[q] / gamma;
+        const double phi = cs[q] * phibar[q];
         phibar[q] = sn[q] * phibar[q];
-        cf[q] = oldeps[q];
-        cf[NR + q] = delta[q];
-        cf[2 * NR + q] = 1.0 / gamma[q];
-        cf[3 * NR + q] = phi[q];
+        cf[q] = oldeps;
+        cf[NR + q] = delta;
+        cf[2 * NR + q] = 1.0 / gamma;
+        cf[3 * NR + q] = phi;
       }
       // w1 <- w2, w2 <- w, w <- (v - oldeps w1 - delta w2) / gamma, dx += phi w
       std::swap(w1, w2);  // w1 <- old w2
