@@ -154,6 +154,8 @@ struct GemmArgs {
   GemmOut out, out2;  // out2 is written too when out2.C or out2.Chi is set
   int *err;
   int ksplit = 1;     // > 1: blockIdx.z takes a share of the K steps and adds into out.C atomically
+  int mt = 1, nt = 1; // M and N tiles; blockIdx.x enumerates them in groups of gm M tiles
+  int gm = 1;
 };
 __device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float x) {
   if (o.C) {
@@ -271,9 +273,18 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // blockIdx.x walks the M tiles: the CTAs resident at one time cover all M tiles of a few N
-  // tiles, so each B tile is fetched from DRAM once and the A operand stays in L2
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // blockIdx.x enumerates the tiles in groups of gm M tiles, M fastest within a group and then
+  // every N tile: the CTAs resident at one time share a few B tiles (each fetched from DRAM
+  // once per group) and the group's A rows, which the host sizes to stay in L2
+  int m0, n0;
+  {
+    const int id = (int)blockIdx.x;
+    const int grp = id / (args.gm * args.nt), first = grp * args.gm;
+    const int gsize = min(args.gm, args.mt - first);
+    const int local = id - grp * args.gm * args.nt;
+    m0 = (first + local % gsize) * BM;
+    n0 = (local / gsize) * BN;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -1079,10 +1090,18 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
   };
   const bool acc = out.C && out.accumulate && !out2;
   const int nk = (int)(K / BK);
+  // M tiles per raster group: the group's A rows (all K steps, every distinct A buffer) within
+  // 64 MB, half of L2; each B tile is then fetched from DRAM once per group
+  const long long a_tile_bytes = (long long)BM * nk * BK * 2 * (nseg == 3 ? 2 : 1);
+  const int gm_rows = (int)std::max<long long>(1, (64LL << 20) / std::max<long long>(a_tile_bytes, 1));
   auto args_for = [&](int bn, int ksplit, dim3 &grid) {
     GemmArgs a{M, N, nk, nseg, out, out2 ? *out2 : GemmOut{}, err};
-    grid = dim3((M + BM - 1) / BM, (N + bn - 1) / bn, 1);
-    if (grid.y > 65535) throw PPError(PP_EINVAL, "k_gemm_bf16: too many N tiles");
+    a.mt = (M + BM - 1) / BM;
+    a.nt = (N + bn - 1) / bn;
+    a.gm = std::min(a.mt, gm_rows);
+    const long long tiles = (long long)a.mt * a.nt;
+    if (tiles > 0x7fffffffLL) throw PPError(PP_EINVAL, "k_gemm_bf16: too many tiles");
+    grid = dim3((unsigned)tiles, 1, 1);
     a.ksplit = ksplit;
     grid.z = (unsigned)ksplit;
     return a;
@@ -1462,7 +1481,9 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   R = std::max<long long>(2, std::min<long long>(R, 64));
   R &= ~1LL;
   p->Rmax = (int)R;
-  p->slab_i = (int)std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
+  // the amplitude slab holds up to 512 MB per BF16 part; each sigma chunk picks its height
+  // (choose_slab) so that the slab GEMM fills whole waves
+  p->slab_i = (int)std::max<long long>(1, std::min<long long>(o, (512LL << 20) / (2 * v * p->ldT)));
   {
     int dev = 0, nsm = 0;
     PP_CUDA(cudaGetDevice(&dev));
@@ -1593,19 +1614,21 @@ void precompute_tc(pp_ctx *c) {
 
 // Occupied rows per slab for one sigma chunk of NC = R Q columns.  The slab GEMM P = T C^T has
 // ceil(ni v / 128) x ceil(NC / 256) tiles at one CTA per SM, so its time goes in whole waves of
-// nsm CTAs (768 tiles at 8 rows and R = 16 are 5.05 waves: the sixth runs 8 CTAs).  The height
-// that minimises the waves over all slabs -- the generator's waves weighted by their cost
-// relative to a GEMM wave, plus a small per-slab launch cost -- is taken, at most si_max.
-static int choose_slab(int o, int v, long long NC, int si_max, int nsm) {
-  const long long nt = (v + 127) / 128, ntn = (NC + 255) / 256;
+// nsm CTAs; the persistent generator covers ni o npairs items (two 128 x 128 x Q products each,
+// about 2 Q / ov of a GEMM tile's time at its lower efficiency) in waves of nsm CTAs.  The
+// height (at most si_max) that minimises the waves over all slabs, plus a small per-slab
+// launch cost, is taken.
+static int choose_slab(int o, int v, int Q, long long NC, int si_max, int nsm) {
+  const long long nt = (v + 127) / 128, npairs = nt * (nt + 1) / 2, ntn = (NC + 255) / 256;
+  const double item = 2.0 * Q / ((double)o * v);
   double best = 1e300;
   int arg = si_max;
   for (int si = si_max; si >= 1; --si) {
     double cost = 0.0;
     for (int i0 = 0; i0 < o; i0 += si) {
       const long long ni = std::min(si, o - i0);
-      const long long gt = (ni * v + 127) / 128 * ntn, tt = nt * nt * o * ni;
-      cost += (double)((gt + nsm - 1) / nsm) + 0.21 * (double)((tt + nsm - 1) / nsm) + 0.05;
+      const long long gt = (ni * v + 127) / 128 * ntn, tt = ni * o * npairs;
+      cost += (double)((gt + nsm - 1) / nsm) + item * (double)((tt + nsm - 1) / nsm) + 0.05;
     }
     if (cost < best - 1e-9) {
       best = cost;
@@ -1793,7 +1816,7 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       bf *tlo = split ? p->t_lo.as<bf>() : nullptr;
       bf *p1h = p->p1_hi.as<bf>(), *p1l = split ? p->p1_lo.as<bf>() : nullptr;
       bf *p2h = p->p2_hi.as<bf>(), *p2l = split ? p->p2_lo.as<bf>() : nullptr;
-      const int si = choose_slab(o, v, NC, p->slab_i, p->nsm);
+      const int si = choose_slab(o, v, Q, NC, p->slab_i, p->nsm);
       for (int i0 = 0; i0 < o; i0 += si) {
         const int ni = std::min(si, o - i0);
         const long long rows = (long long)ni * v;
