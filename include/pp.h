@@ -187,7 +187,8 @@ pp_status pp_solve_window(pp_ctx *ctx, double omega0, double delta, int k, doubl
  * repeated until every Ritz pair in the window meets res_tol (at most min(max_iter, 60)
  * filter applications).  The block holds 1.5 times the diagonal's count of roots in the window
  * plus 4, at most 64 vectors (PP_EINVAL for wider windows).  Mixed contexts filter with the
- * BF16 sigma and take Rayleigh-Ritz products with the split form.
+ * BF16 sigma until the worst in-window residual gains less than 2x per filter application,
+ * then with the split form; their Rayleigh-Ritz products are always split-form.
  *   omega, osc, resid: host outputs of capacity k, ascending; *nfound: the roots in the window
  *   (PP_EINVAL if more than k).  PP_ENOTCONV with the last estimates if the limit is reached.
  */
@@ -210,7 +211,8 @@ pp_status pp_solve_windows(pp_ctx *ctx, int nwin, const double *omega0, const do
  * over the positive roots (so the trace / 3 is sum_n f_n / (omega_n^2 - omega_f^2)).  The
  * three systems per frequency are solved by preconditioned MINRES with the Jacobi diagonal
  * |diag(M - omega Sigma)| (floored at jacobi_floor) as preconditioner; mixed contexts refine
- * on the residual (split-BF16 residuals, BF16 corrections), FP64 contexts run in FP64.
+ * on the residual (split-BF16 residuals; BF16 corrections, switched to the split form once
+ * an outer step gains less than 4x, as near a root), FP64 contexts run in FP64.
  *   omega[nfreq]: host frequencies (Ha); off resonance (a frequency at a root is singular).
  *   tol: relative residual |F - K x| / |F| to reach; max_iter: MINRES iterations per frequency.
  *   alpha: host [nfreq][3][3]; resid (may be NULL): host [nfreq], the final relative residual

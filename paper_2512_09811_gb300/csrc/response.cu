@@ -13,8 +13,10 @@
 //
 // Arithmetic.  FP64 contexts: one MINRES run with the FP64 sigma.  Mixed contexts: iterative
 // refinement on the residual -- the outer residual r = F - K x is formed with the split-BF16
-// (FP32-level) sigma, and each correction K d = r is solved by MINRES with the BF16 sigma to
-// a relative residual of 1e-2 (or the requested tolerance, if that is looser); x += d.
+// sigma, and each correction K d = r is solved by MINRES to a relative residual of 1e-2 (or
+// the requested tolerance, if that is looser); x += d.  The corrections use the BF16 sigma
+// until an outer step reduces the residual by less than 4x (near a root, where cond(K) times
+// the BF16 operator error nears 1), then the split form.
 #include "pp_internal.h"
 
 #include <algorithm>
@@ -269,8 +271,13 @@ pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double 
       PP_CUDA(cudaMemsetAsync(lr.x, 0, sizeof(double) * NR * L, s));
       PP_CUDA(cudaMemcpyAsync(lr.r, lr.F, sizeof(double) * NR * L, cudaMemcpyDeviceToDevice, s));
       const double inner = std::max(tol, 1e-2);
+      // the BF16 corrections contract the residual by about cond(K) x (BF16 operator error);
+      // near a root that factor approaches 1, and the corrections switch to the split form
+      // (the operator of the residual itself) once an outer step gains less than 4x
+      int p_inner = PP_BF16;
+      double rel_prev = 0.0;
       for (int outer = 0; outer < 20 && its < max_iter; ++outer) {
-        if (outer > 0) {  // r = F - K x with the split (FP32-level) sigma
+        if (outer > 0) {  // r = F - K x with the split sigma
           lr.apply(lr.x, lr.r, w, p_acc);
           const double cf[2 * NR] = {1, 1, 1, -1, -1, -1};
           lr.set_coef(cf, 2 * NR);
@@ -282,7 +289,9 @@ pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double 
         rel = 0.0;
         for (int q = 0; q < NR; ++q) rel = std::max(rel, std::sqrt(rn[q] / std::max(fn[q], 1e-300)));
         if (rel <= tol) break;
-        its += lr.minres(lr.r, lr.d, w, PP_BF16, inner, max_iter - its);
+        if (outer > 0 && rel > 0.25 * rel_prev) p_inner = p_acc;
+        rel_prev = rel;
+        its += lr.minres(lr.r, lr.d, w, p_inner, inner, max_iter - its);
         const double cf[2 * NR] = {1, 1, 1, 1, 1, 1};
         lr.set_coef(cf, 2 * NR);
         k_lr_axpby<<<ew_blocks(NR * L), 256, 0, s>>>(lr.x, lr.d, lr.coef, L);  // x += d

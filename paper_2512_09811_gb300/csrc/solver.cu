@@ -2173,7 +2173,12 @@ pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0_r
   const long long ov = c->ov, L = 2 * ov;
   const double ctr = omega0 + 0.5 * delta, rad = 0.5 * delta;
   const bool mixed = c->opt.prec != PP_FP64;
-  const int p_filter = mixed ? PP_BF16 : PP_FP64, p_acc = mixed ? PP_BF16X3 : PP_FP64;
+  const int p_acc = mixed ? PP_BF16X3 : PP_FP64;
+  // the filter projects onto the invariant subspace of the operator it applies: the BF16 one
+  // stalls at its own operator error, so a mixed context filters with the split form once the
+  // worst in-window residual gains less than 2x in an outer iteration
+  int p_filter = mixed ? PP_BF16 : PP_FP64;
+  double worst_prev = 0.0;
   // subspace size: 1.5 x the diagonal estimate of the roots in the window, plus a margin
   std::vector<double> hA(ov), hS(ov);
   PP_CUDA(cudaMemcpyAsync(hA.data(), c->diagA.p, sizeof(double) * ov, cudaMemcpyDeviceToHost, s));
@@ -2250,8 +2255,7 @@ pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0_r
     PP_CUDA(cudaStreamSynchronize(s));
   }
   // inner tolerance: the outer residual settles near 2e-3 times it (CPU emulation); BF16 filters
-  // cannot go much below 1e-4 (their operator error is ~1e-5)
-  const double tol_in = mixed ? 1e-4 : 1e-6;
+  // cannot go much below 1e-4 (their operator error is ~1e-5), split and FP64 ones go to 1e-6
   const int max_in = 300;  // inner iterations per filter application (tens suffice here)
   std::vector<double> th_prev;
   std::vector<double> h_th, h_res, h_xsx;
@@ -2312,7 +2316,7 @@ pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0_r
         if (!done[t] && std::sqrt(hd[3 * t + 2]) > 0.0) {
           // |r| from the same reduction: |r|^2 is the third output of the (r, z) dot
           const double rn = std::sqrt(hd[3 * t + 2]);
-          if (rn <= tol_in * bn[t]) done[t] = 1;
+          if (rn <= (p_filter == PP_BF16 ? 1e-4 : 1e-6) * bn[t]) done[t] = 1;
         }
         const double nr = hd[3 * t], ni = hd[3 * t + 1];
         const double den = rho_r[t] * rho_r[t] + rho_i[t] * rho_i[t];
@@ -2406,17 +2410,19 @@ pp_status riesz_impl(pp_ctx *c, double omega0, double delta, int nquad, int m0_r
     std::vector<double> th_now;
     for (int j : sel) th_now.push_back(h_th[j]);
     std::sort(th_now.begin(), th_now.end());
-    if (const char *e = std::getenv("PP_LOG"); e && e[0] && e[0] != '0') {
-      double worst = 0.0;
-      for (int j : sel) worst = std::max(worst, h_res[j]);
-      std::fprintf(stderr, "[pp] contour it %d m %d in-window %zu worst %.2e\n", outer, m, sel.size(), worst);
-    }
+    double worst = 0.0;
+    for (int j : sel) worst = std::max(worst, h_res[j]);
+    if (const char *e = std::getenv("PP_LOG"); e && e[0] && e[0] != '0')
+      std::fprintf(stderr, "[pp] contour it %d m %d in-window %zu worst %.2e filter %d\n", outer, m, sel.size(), worst,
+                   p_filter);
     // converged: every Ritz value in the window meets the tolerance and the count is stable
     if (conv && th_now.size() == th_prev.size()) {
       status = PP_OK;
       break;
     }
     th_prev = th_now;
+    if (p_filter == PP_BF16 && outer > 0 && worst > 0.5 * worst_prev) p_filter = PP_BF16X3;
+    worst_prev = worst;
     if (m < m0) {  // refill the block to m0 with unit vectors (the filter needs m0 >= roots inside)
       PP_CUDA(cudaMemsetAsync(Y + (long long)m * L, 0, vec * (m0 - m), s));
     }

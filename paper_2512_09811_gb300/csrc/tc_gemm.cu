@@ -1900,14 +1900,14 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
   // the profiling events are recorded.
   const bool graphs = c->opt.graphs != 0 && !p->prof.on;
   if (graphs) {
-    const size_t sig = chunk_buffers_signature(p);
+    p->g_in.ensure(sizeof(double) * (size_t)Rmax * ov);
+    p->g_sig.ensure(sizeof(double) * (size_t)Rmax * ov);
+    p->g_met.ensure(sizeof(double) * (size_t)Rmax * ov);
+    const size_t sig = chunk_buffers_signature(p);  // after every buffer a capture reads is in place
     if (sig != p->graph_sig) {  // workspaces reallocated since the graphs were captured
       clear_chunk_graphs(p);
       p->graph_sig = sig;
     }
-    p->g_in.ensure(sizeof(double) * (size_t)Rmax * ov);
-    p->g_sig.ensure(sizeof(double) * (size_t)Rmax * ov);
-    p->g_met.ensure(sizeof(double) * (size_t)Rmax * ov);
   }
   for (int r0 = 0; r0 < R_total; r0 += Rmax) {
     const int R = std::min(Rmax, R_total - r0);

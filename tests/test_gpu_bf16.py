@@ -87,8 +87,9 @@ def test_sigma_chunk_graphs_replay(cuda_lib):
             for call in range(3):
                 got, met = graph.sigma(Z, prec=prec, metric=True)
                 assert np.abs(got - base).max() <= 1e-6 * np.abs(base).max(), (name, call)
-                # two contexts: their FP32 split-K pair sums differ in the last bits
-                assert np.abs(met - base_m).max() <= 1e-8 * np.abs(base_m).max()
+                # two contexts: their pair sums (FP32, split-K atomics) differ by a few FP32 ulps
+                # (the metric reads them in FP64: 5.7e-8 of its largest element was measured)
+                assert np.abs(met - base_m).max() <= 1e-6 * np.abs(base_m).max()
                 r, at = elementwise_ok(got, want, scale, name)
                 assert r <= 1.0, (name, call, r, at)
             # the same shape without the metric output is a different graph
