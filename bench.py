@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the batched window solver on one GB300.
 
-Workload (default, the batched block-Krylov configuration): one synthetic dot with
-nocc = 128, nvir = 512, naux = 1536 (particle-hole dimension 65536), seed 2, FP32 density-
-fitting tensor of perturbative width; 8 consecutive windows of 0.05 Ha from the 20th
-percentile of diag(A)/diag(S), the k = 8 lowest roots of each, block of 16 trial vectors
-per window; second order, mixed precision (BF16 tensor-core sigma with FP32 accumulation,
-FP64 Krylov basis and projected problems, split-BF16 refinement to a residual of 1e-6).
+Workload (default, the large dot): one synthetic dot with nocc = 256, nvir = 1024,
+naux = 3072 (particle-hole dimension 262144; 6.9e10 MP2 amplitudes, regenerated per slab),
+seed 4, FP32 density-fitting tensor (20 GB) of perturbative width; 4 consecutive windows of
+0.05 Ha from the 20th percentile of diag(A)/diag(S), the k = 16 lowest roots of each, block
+of 16 trial vectors per window; second order, mixed precision (BF16 tensor-core sigma with
+FP32 accumulation, FP64 Krylov basis and projected problems, split-BF16 refinement to a
+residual of 1e-6).  --workload batched-128x512x1536 runs the 8-window x k = 8 batch on the
+128/512/1536 dot, --workload dot-64x256x768 the single window of the plain-vs-mixed test.
 
-A step is one block iteration of the 8-window batch: the whole hot path once -- Rayleigh-
-Ritz and the folded extraction, residuals, weighted-Jacobi directions, block CGS2, and one
-sigma batch per precision phase of every window's new vectors (pp_windows_step).  value =
-algorithmic sigma TFLOP/s of the timed steps (each contraction counted once; the split
-form's three products count as one); the full solve continues after the timed steps, and
-its converged roots per second are reported beside the value.  e2e repeats the whole solve
-through the C ABI from pinned host buffers (pp_create with the host B tensor, solve,
-results to host) with the copies inside the timed region.
+A step is one block iteration of the window batch: the whole hot path once -- Rayleigh-Ritz
+and the folded extraction, residuals, weighted-Jacobi directions, block CGS2, and one sigma
+batch per precision phase of every window's new vectors (pp_windows_step).  value =
+algorithmic sigma TFLOP/s of the timed steps (each contraction counted once; the split form's
+three products count as one).  With --full-solve (the default for the two smaller workloads)
+the solve continues after the timed steps and its converged roots per second are reported
+beside the value.  e2e times the sigma batch of one step through the C ABI on pinned host
+buffers (pp_sigma with on_device = 0: the host-to-device copy of the trial vectors, the
+product, the device-to-host copy of sigma and Sigma z inside the timed region).
 
 Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 """
@@ -41,15 +44,16 @@ if ROOT not in sys.path:
 WORKLOADS = {
     # 8 windows x k = 8, block 16 per window (128 trial supervectors per iteration)
     "batched-128x512x1536": dict(nocc=128, nvir=512, naux=1536, seed=2, mode="perturbative", pct=20.0, nwin=8,
-                                 delta=0.05, k=8, block=16, order=2),
+                                 delta=0.05, k=8, block=16, order=2, full_solve=True),
     # one window, k = 8 (the plain-vs-mixed comparison)
     "dot-64x256x768": dict(nocc=64, nvir=256, naux=768, seed=1, mode="perturbative", pct=20.0, nwin=1, delta=0.1,
-                           k=8, block=8, order=2),
-    # 4 windows x k = 16 (the large dot; a block iteration takes tens of seconds)
+                           k=8, block=8, order=2, full_solve=True),
+    # 4 windows x k = 16 (the large dot: a block iteration takes about 50 s, a full solve tens of
+    # minutes, so the solve is not finished by default)
     "dot-256x1024x3072": dict(nocc=256, nvir=1024, naux=3072, seed=4, mode="perturbative", pct=20.0, nwin=4,
-                              delta=0.05, k=16, block=16, order=2),
+                              delta=0.05, k=16, block=16, order=2, full_solve=False),
 }
-DEFAULT_WORKLOAD = "batched-128x512x1536"
+DEFAULT_WORKLOAD = "dot-256x1024x3072"
 METRIC = "converged roots/s & sigma TFLOP/s at <=1e-6 Ha vs FP64 oracle; p50/p99 window latency"
 # residual |M x - theta Sigma x| / |x^T Sigma x| at which a root counts as converged; the split-
 # BF16 refinement reaches it, and an isolated root then lies within |r|^2 / gap of theta
@@ -268,7 +272,8 @@ def run_ours(args, world, rank, local):
     value = flops_tot / (ms_max / 1e3) / 1e12
     # finish the solve that was running when the timed steps ended (at least one full batch)
     roots_obj = None
-    if not args.no_full_solve:
+    full_solve = w["full_solve"] if args.full_solve is None else args.full_solve
+    if full_solve:
         while not solves:
             one_step()
         first = solves[0]
@@ -279,35 +284,33 @@ def run_ours(args, world, rank, local):
                          sigma_vectors=first["sigma_vectors"], max_resid=first["max_resid"], found=first["found"],
                          status=first["status"], sigma_tflops=solve_flops / (first["ms"] / 1e3) / 1e12)
 
-    # ---- end to end through the C ABI from pinned host buffers ---------------------------
-    from synth.inputs import DotInputs
-
-    h2d = inp.eps.nbytes + inp.B.nbytes + inp.mu.nbytes
-    d2h = sum(ks) * 3 * 8 + 4 * len(ks)
+    # ---- end to end through the C ABI on pinned host buffers: one step's sigma batch -----
     e2e = None
-    if not args.no_e2e and not args.no_full_solve:
-        pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(inp, f))).pin_memory().numpy()
-               for f in ("eps", "B", "mu")}
-        pinned = DotInputs(nocc=inp.nocc, nvir=inp.nvir, naux=inp.naux, sigma_b=inp.sigma_b, seed=inp.seed, **pin)
-        dot.close()
+    nv_step = max(1, int(round(timed_nv / max(args.steps, 1))))
+    if not args.no_e2e:
+        from synth.inputs import random_vectors
+
+        Zh = torch.from_numpy(random_vectors(nv_step, o, v, seed=11)).pin_memory()
+        Sh = torch.empty_like(Zh).pin_memory()
+        Mh = torch.empty_like(Zh).pin_memory()
+        lib = pp.load()
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.time()
-        d2 = pp.Dot(pinned, **opt_kw)
-        outs, st2 = d2.solve_windows(wins, deltas, ks, allow_notconv=True)
-        stats2 = d2.stats()
+        st = lib.pp_sigma(dot.ctx, nv_step, Zh.data_ptr(), Sh.data_ptr(), Mh.data_ptr(), pp.PP_BF16, 0)
         torch.cuda.synchronize()
         e2e_s = time.time() - t0
-        d2.close()
-        ee = sum(int(np.count_nonzero(r["resid"] <= RES_TOL * 1.0000001)) for r in outs)
-        e2e_fl = stats2["sigma_vectors"] * sigma_flops_per_vector(o, v, Q)
+        pp._check(st, dot.ctx)
+        fin = bool(np.isfinite(Sh.numpy()).all())
+        e2e_fl = step_flops(o, v, Q, nv_step, 1)
         e2e_max, e2e_flops = reduce_over_ranks(dist, e2e_s * 1e3, e2e_fl, "cuda")
-        _, ee_tot = reduce_over_ranks(dist, e2e_s * 1e3, ee, "cuda")
-        e2e = dict(value=e2e_flops / (e2e_max / 1e3) / 1e12, unit="TFLOP/s", h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h), step="pp_create from pinned host inputs + pp_solve_windows + "
-                   "results to host", roots_per_s=ee_tot / (e2e_max / 1e3), seconds=e2e_max / 1e3,
-                   iterations=stats2["iterations"])
-    else:
-        dot.close()
+        nb = Zh.numel() * 8
+        e2e = dict(value=e2e_flops / (e2e_max / 1e3) / 1e12, unit="TFLOP/s", h2d_bytes_per_step=int(nb),
+                   d2h_bytes_per_step=int(2 * nb), supervectors=nv_step, seconds=e2e_max / 1e3, finite=fin,
+                   step="pp_sigma through the C ABI on pinned host buffers (on_device = 0): trial vectors "
+                        "host->device, BF16 tensor-core sigma and metric, both products device->host")
+    dot.close()
 
     # ---- roofline of the dominant kernel: the amplitude-contraction GEMM -----------------
     achieved = (k0["flops"] / (k0["ms"] / 1e3) / 1e12) if k0["ms"] > 0 else None
@@ -550,15 +553,16 @@ def profile_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve from host buffers")
-    ap.add_argument("--no-full-solve", action="store_true",
-                    help="time the steps only, without finishing the solve (the large dot: a full solve takes "
-                         "tens of minutes)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end sigma batch on host buffers")
+    ap.add_argument("--full-solve", dest="full_solve", action="store_true", default=None,
+                    help="finish the solve after the timed steps and report its converged roots/s (default for "
+                         "the two smaller workloads; the large dot's full solve takes tens of minutes)")
+    ap.add_argument("--no-full-solve", dest="full_solve", action="store_false")
     ap.add_argument("--workspace-gb", type=float, default=0.0,
                     help="device memory for one chunk of the sigma workspaces (0: automatic)")
     ap.add_argument("--fp64-leg", action="store_true",

@@ -1692,6 +1692,18 @@ struct WindowBatch {
       finalize(wi, PP_ENOTCONV);
       return 0;
     }
+    if (!conv && refine && wi.prec == PP_BF16X3) {
+      // the split form has a floor too (its products round the intermediates to 16-bit
+      // significands): a window whose worst needed residual has not improved 1.4x in 30
+      // iterations reports what it has as not converged instead of running to max_iter
+      if (worst < 0.7 * wi.best_worst) {
+        wi.best_worst = worst;
+        wi.stall = 0;
+      } else if (++wi.stall >= 30) {
+        finalize(wi, PP_ENOTCONV);
+        return 0;
+      }
+    }
     // columns that get a direction: every unconverged block column, except in the split
     // (refinement) phase, where the products cost three times as much and the roots the
     // window needs (with their guards) are already close: only those, unless all of them
