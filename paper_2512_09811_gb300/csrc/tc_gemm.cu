@@ -154,8 +154,7 @@ struct GemmArgs {
   GemmOut out, out2;  // out2 is written too when out2.C or out2.Chi is set
   int *err;
   int ksplit = 1;     // > 1: blockIdx.z takes a share of the K steps and adds into out.C atomically
-  int mt = 1, nt = 1; // M and N tiles; blockIdx.x enumerates them in groups of gm M tiles
-  int gm = 1;
+  int mt = 1, nt = 1; // M and N tiles; blockIdx.x enumerates them, M fastest
 };
 __device__ __forceinline__ void epi_store(const GemmOut &o, long long off, float x) {
   if (o.C) {
@@ -273,18 +272,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ Ge
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // blockIdx.x enumerates the tiles in groups of gm M tiles, M fastest within a group and then
-  // every N tile: the CTAs resident at one time share a few B tiles (each fetched from DRAM
-  // once per group) and the group's A rows, which the host sizes to stay in L2
-  int m0, n0;
-  {
-    const int id = (int)blockIdx.x;
-    const int grp = id / (args.gm * args.nt), first = grp * args.gm;
-    const int gsize = min(args.gm, args.mt - first);
-    const int local = id - grp * args.gm * args.nt;
-    m0 = (first + local % gsize) * BM;
-    n0 = (local / gsize) * BN;
-  }
+  // blockIdx.x walks the M tiles fastest: the CTAs resident at one time cover every M tile of
+  // a few N tiles, so each B tile is fetched from DRAM once, and an A operand that fits in L2
+  // (the host keeps the amplitude slab of a wide GEMM within 64 MB) is read from DRAM once
+  const int m0 = (int)(blockIdx.x % (unsigned)args.mt) * BM, n0 = (int)(blockIdx.x / (unsigned)args.mt) * BN;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -1090,15 +1081,10 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
   };
   const bool acc = out.C && out.accumulate && !out2;
   const int nk = (int)(K / BK);
-  // M tiles per raster group: the group's A rows (all K steps, every distinct A buffer) within
-  // 64 MB, half of L2; each B tile is then fetched from DRAM once per group
-  const long long a_tile_bytes = (long long)BM * nk * BK * 2 * (nseg == 3 ? 2 : 1);
-  const int gm_rows = (int)std::max<long long>(1, (64LL << 20) / std::max<long long>(a_tile_bytes, 1));
   auto args_for = [&](int bn, int ksplit, dim3 &grid) {
     GemmArgs a{M, N, nk, nseg, out, out2 ? *out2 : GemmOut{}, err};
     a.mt = (M + BM - 1) / BM;
     a.nt = (N + bn - 1) / bn;
-    a.gm = std::min(a.mt, gm_rows);
     const long long tiles = (long long)a.mt * a.nt;
     if (tiles > 0x7fffffffLL) throw PPError(PP_EINVAL, "k_gemm_bf16: too many tiles");
     grid = dim3((unsigned)tiles, 1, 1);
@@ -1287,6 +1273,7 @@ struct TcPlan {
   bool ready = false;  // copies of the per-dot intermediates made (after the precompute)
   KernelProfile prof;
   int slab_i = 1, Rmax = 2;  // slab_i: occupied rows of the largest slab the buffers hold
+  int slab_l2 = 1;           // occupied rows of a slab within 64 MB per BF16 part (stays in L2)
   int nsm = 152;             // SMs of the device (waves of the slab GEMM)
   // BF16 hi/lo operands (K-major, K padded to 64)
   DevBuf bovT_hi, bovT_lo;   // [(i,a)][ldq]       amplitude slab generator
@@ -1482,8 +1469,11 @@ static TcPlan *tc_plan_operands(pp_ctx *c) {
   R &= ~1LL;
   p->Rmax = (int)R;
   // the amplitude slab holds up to 512 MB per BF16 part; each sigma chunk picks its height
-  // (choose_slab) so that the slab GEMM fills whole waves
+  // (choose_slab): within 64 MB per part when its C_Q(V) operand is large (the slab is the
+  // GEMM's A operand and must stay in L2 while C_Q(V) streams past it once), larger only for
+  // narrow chunks, whose few N tiles would otherwise leave most SMs idle
   p->slab_i = (int)std::max<long long>(1, std::min<long long>(o, (512LL << 20) / (2 * v * p->ldT)));
+  p->slab_l2 = (int)std::max<long long>(1, std::min<long long>(o, (64LL << 20) / (2 * v * p->ldT)));
   {
     int dev = 0, nsm = 0;
     PP_CUDA(cudaGetDevice(&dev));
@@ -1541,7 +1531,7 @@ void precompute_tc(pp_ctx *c) {
     using bf = __nv_bfloat16;
     TcPlan *p = tc_plan_operands(c);
     const long long ldT = p->ldT;
-    const int si = p->slab_i;
+    const int si = p->slab_l2;
     p->t_hi.ensure(sizeof(bf) * (size_t)si * v * ldT);
     p->t_lo.ensure(sizeof(bf) * (size_t)si * v * ldT);
     DevBuf T32, Tw32, acc, bk_hi, bk_lo;
@@ -1816,7 +1806,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
       bf *tlo = split ? p->t_lo.as<bf>() : nullptr;
       bf *p1h = p->p1_hi.as<bf>(), *p1l = split ? p->p1_lo.as<bf>() : nullptr;
       bf *p2h = p->p2_hi.as<bf>(), *p2l = split ? p->p2_lo.as<bf>() : nullptr;
-      const int si = choose_slab(o, v, Q, NC, p->slab_i, p->nsm);
+      const long long cq_bytes = NC * ldT * 2 * (split ? 2 : 1);  // the streamed operand
+      const int si = choose_slab(o, v, Q, NC, cq_bytes <= (2LL << 30) ? p->slab_i : p->slab_l2, p->nsm);
       for (int i0 = 0; i0 < o; i0 += si) {
         const int ni = std::min(si, o - i0);
         const long long rows = (long long)ni * v;
