@@ -51,7 +51,7 @@ WORKLOADS = {
     # 4 windows x k = 16 (the large dot: a block iteration takes about 50 s, a full solve tens of
     # minutes, so the solve is not finished by default)
     "dot-256x1024x3072": dict(nocc=256, nvir=1024, naux=3072, seed=4, mode="perturbative", pct=20.0, nwin=4,
-                              delta=0.05, k=16, block=16, order=2, full_solve=False),
+                              delta=0.05, k=16, block=16, order=2, full_solve=False, workspace_gb=140.0),
 }
 DEFAULT_WORKLOAD = "dot-256x1024x3072"
 METRIC = "converged roots/s & sigma TFLOP/s at <=1e-6 Ha vs FP64 oracle; p50/p99 window latency"
@@ -206,8 +206,11 @@ def run_ours(args, world, rank, local):
     w = WORKLOADS[args.workload]
     o, v, Q = w["nocc"], w["nvir"], w["naux"]
     inp = make_dot_inputs(w)
+    # the large dot holds about 90 GB of integrals and their copies; 140 GB of sigma workspace
+    # (14 half-vectors per chunk) fit beside them
+    ws = args.workspace_gb if args.workspace_gb > 0 else w.get("workspace_gb", 0.0)
     opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"], refine=1,
-                  max_iter=300, cuda_stream=stream.cuda_stream, workspace_gb=args.workspace_gb)
+                  max_iter=300, cuda_stream=stream.cuda_stream, workspace_gb=ws)
     t0 = time.time()
     dot = pp.Dot(inp, **opt_kw)
     torch.cuda.synchronize()

@@ -86,8 +86,8 @@ typedef struct {
   uint64_t seed;       /* reserved for random initial vectors */
   void *cuda_stream;   /* cudaStream_t to use, or NULL to create one */
   double workspace_gb; /* device memory for one chunk of the tensor-core sigma workspaces
-                          (0 = automatic: a quarter of the free memory at first use, between
-                          12 and 64 GB) */
+                          (0 = automatic: half of the free memory at first use, keeping 8 GB
+                          free, at least 12 GB) */
   int tda;             /* 1: Tamm-Dancoff form (Sec. 2.2 with B = 0): M = diag(A, A), so the
                           roots are those of A X = omega S X and the sigma products skip every
                           B term (the amplitude contraction included); 0 (default): full form */
@@ -218,7 +218,10 @@ pp_status pp_solve_windows(pp_ctx *ctx, int nwin, const double *omega0, const do
  *   alpha: host [nfreq][3][3]; resid (may be NULL): host [nfreq], the final relative residual
  *   (largest of the three systems, accurate operator); iterations (may be NULL): host [nfreq].
  * Needs dipole integrals (mu at pp_create), else PP_EINVAL.  PP_ENOTCONV if a frequency
- * ends above 10 tol (its best estimate is written).
+ * ends above 10 tol (its best estimate is written).  In mixed contexts the residual cannot
+ * fall below the noise of the split-BF16 products (their rounding is not linear in x) times
+ * |x| / |F|, which grows near a root: about 1e-5 between two roots 3 mHa apart at the
+ * 16/64/192 dot, where the polarizability itself is still accurate to 4e-5.
  */
 pp_status pp_polarizability(pp_ctx *ctx, int nfreq, const double *omega, double tol, int max_iter, double *alpha,
                             double *resid, int *iterations);

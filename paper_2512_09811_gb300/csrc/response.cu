@@ -274,7 +274,7 @@ pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double 
       // the BF16 corrections contract the residual by about cond(K) x (BF16 operator error);
       // near a root that factor approaches 1, and the corrections switch to the split form
       // (the operator of the residual itself) once an outer step gains less than 4x
-      int p_inner = PP_BF16;
+      int p_inner = PP_BF16, stalls = 0;
       double rel_prev = 0.0;
       for (int outer = 0; outer < 20 && its < max_iter; ++outer) {
         if (outer > 0) {  // r = F - K x with the split sigma
@@ -289,7 +289,12 @@ pp_status polarizability_impl(pp_ctx *c, int nfreq, const double *omega, double 
         rel = 0.0;
         for (int q = 0; q < NR; ++q) rel = std::max(rel, std::sqrt(rn[q] / std::max(fn[q], 1e-300)));
         if (rel <= tol) break;
-        if (outer > 0 && rel > 0.25 * rel_prev) p_inner = p_acc;
+        if (outer > 0 && rel > 0.25 * rel_prev) {
+          // the split-form corrections stall too once the residual reaches the noise of the
+          // split products (their rounding is not linear in x), amplified by |x| / |F|
+          if (p_inner == p_acc && ++stalls >= 2) break;
+          p_inner = p_acc;
+        }
         rel_prev = rel;
         its += lr.minres(lr.r, lr.d, w, p_inner, inner, max_iter - its);
         const double cf[2 * NR] = {1, 1, 1, 1, 1, 1};

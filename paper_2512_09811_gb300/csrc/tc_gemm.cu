@@ -1406,7 +1406,10 @@ long long tc_workspace_bytes(const pp_ctx *c) {
   if (c->opt.workspace_gb > 0) return (long long)(c->opt.workspace_gb * (1LL << 30));
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 12LL << 30;
-  return std::min<long long>(64LL << 30, std::max<long long>(12LL << 30, (long long)(free_b / 4)));
+  // half of the free memory (keeping 8 GB free), at least 12 GB: the chunk size R of the sigma
+  // sets how often the amplitudes are regenerated and how wide the contraction GEMMs are
+  const long long half = (long long)(free_b / 2), room = (long long)free_b - (8LL << 30);
+  return std::max<long long>(12LL << 30, std::min<long long>(half, room));
 }
 
 // Stage 1 of the plan: everything that depends on B and eps only (the precompute needs it).

@@ -27,8 +27,10 @@ def test_polarizability_matches_dense(cuda_lib, order):
     freqs = [0.5 * om[0], 0.5 * (om[n] + om[n + 1])]
     want = np.array([po.polarizability(M, Sig, inp.mu, w) for w in freqs])
     # mixed form: the split operator differs from the FP64 one by ~3e-8 relative, amplified near
-    # a root by |omega_n| / (gap / 2) in alpha (~5e-5 at the mid-gap frequency here)
-    for prec_name, tol, rtol in (("PP_FP64", 1e-10, 1e-8), ("PP_BF16", 1e-8, 2e-4)):
+    # a root by |omega_n| / (gap / 2) in alpha (~5e-5 at the mid-gap frequency here); its
+    # residual stops near 1e-5 there (split-product noise times |x| / |F|, measured 6e-6 and
+    # 1.1e-5), so the mixed form is asked for 1e-5
+    for prec_name, tol, rtol in (("PP_FP64", 1e-10, 1e-8), ("PP_BF16", 1e-5, 2e-4)):
         dot = pp.Dot(inp, order=order, prec=getattr(pp, prec_name))
         try:
             out = dot.polarizability(freqs, tol=tol, max_iter=4000)
