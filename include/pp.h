@@ -69,7 +69,8 @@ typedef enum {
                     accumulation, the other contractions in FP32; Krylov basis, projected
                     problem, fold centres and residuals stay FP64 */
   PP_BF16X3 = 3  /* as PP_BF16 with every tensor-core operand split into a BF16 pair
-                    (hi + lo, three products): FP32-level products, used to refine */
+                    (hi + lo, three products): 16-bit significands, about 2^-16
+                    relative error per product, used to refine */
 } pp_precision;
 
 typedef struct {

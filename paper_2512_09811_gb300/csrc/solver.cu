@@ -1736,7 +1736,7 @@ struct WindowBatch {
   }
 
   // refinement: restart the window on its folded target vectors and recompute their
-  // products with the split (FP32-level) tensor-core sigma
+  // products with the split (three-product) tensor-core sigma
   void switch_to_split(Window &wi) {
     const int m = wi.m, b = wi.bx;
     const int nsel = std::min(m, std::max(b, std::min(64, 2 * b)));

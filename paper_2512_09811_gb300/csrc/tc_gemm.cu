@@ -8,7 +8,8 @@
 // epilogue (BF16 out), then consumed by a long-K BF16 GEMM whose FP32
 // accumulator lives in TMEM.  Only one slab of t (a few occupied indices) is
 // alive at any time, in an L2-sized staging buffer; t is never stored whole.
-// Split-BF16 ("bf16x3") operands give FP32-level products for the refinement.
+// Split-BF16 ("bf16x3") operands (hi + lo, three products) give products with 16-bit
+// significands (about 2^-16 relative error each) for the refinement.
 //
 // Kernel structure (both kernels): 128 threads; warp 0 lane 0 issues TMA loads
 // into a STAGES-deep ring of 128B-swizzled shared tiles, warp 1 lane 0 issues
@@ -1639,7 +1640,7 @@ static void ensure_zeroed(DevBuf &b, size_t bytes, cudaStream_t s) {
 
 // BF16 tensor-core sigma: amplitude contraction and the large first-order contractions on
 // tcgen05; the remaining small contractions in FP32.  split = true uses hi/lo BF16 pairs
-// (three products) for an FP32-level result.
+// (three products) for a result with about 2^-16 relative error per product.
 void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *met_d, bool split) {
   TcPlan *p = tc_plan(c);
   tc::prepare_kernels();
@@ -1703,7 +1704,8 @@ void sigma_bf16(pp_ctx *c, int nvec, const double *Zd, double *sig_d, double *me
     // The first-order block on the tensor cores; its operands are written by the GEMMs that
     // produce them in the K-major layouts the next GEMM reads.  These contractions are small
     // next to the amplitude contraction and always run in the split form (three BF16
-    // products, FP32-level), so the BF16 phase keeps its first-order terms at that accuracy.
+    // products, about 2^-16 per product), so the BF16 phase keeps its first-order terms at
+    // that accuracy.
     hk.first_order = [&](int Rc, float *Aacc, float *Bacc) {
       const int nseg1 = 3;
       const int order = c->opt.order;
