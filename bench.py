@@ -544,7 +544,7 @@ def profile_workload(args):
         torch.cuda.synchronize()
     else:
         dot = pp.Dot(inp, prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"],
-                     max_iter=args.profile_solve, graphs=0)
+                     max_iter=args.profile_solve, graphs=0, workspace_gb=w.get("workspace_gb", 0.0))
         dA, dS = dot.diagonal()
         omega0 = float(np.percentile((dA / dS).ravel(), w["pct"]))
         dot.solve_windows(windows_for_rank(omega0, w["delta"], w["nwin"], 0), [w["delta"]] * w["nwin"],
