@@ -1059,6 +1059,19 @@ static int default_ksplit(long long tiles, long long steps) {
   long long ks = std::min<long long>(304 / std::max<long long>(tiles, 1), steps / 8);
   return (int)std::max<long long>(1, std::min<long long>(ks, 65535));
 }
+// K split of an accumulating GEMM, from its reduction length alone: each split sums at most
+// ACC_STEPS K steps (4 ACC_STEPS MMA accumulations into one FP32 TMEM element) before its partial
+// is added into the output.  It depends on K only, so one output element is summed in the same
+// order whatever the chunk shape (M) around it -- the reduced-precision sigma of a vector does
+// not change with the batch it is computed in -- and the FP32 rounding of the longest
+// reductions (the exchange and P contractions, up to millions of terms) is that of chains of
+// at most 4 ACC_STEPS accumulations (about 2e-6 relative), below the 2^-16 of the BF16-pair
+// operands.  Short reductions fall back to the wave-filling rule.
+constexpr long long ACC_STEPS = 512;
+static int acc_ksplit(long long tiles, long long steps) {
+  if (steps <= ACC_STEPS) return default_ksplit(tiles, steps);
+  return (int)std::min<long long>((steps + ACC_STEPS - 1) / ACC_STEPS, 65535);
+}
 
 // out (+)= alpha * sum_seg A_seg B_seg^T; segments share M, N, K; output addressing per GemmOut.
 // site names the contraction for the autotuner; acc_base / acc_bytes give the region an
@@ -1096,7 +1109,7 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
   auto ks_for = [&](int bn) {
     if (!acc) return 1;
     const long long tiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn);
-    return default_ksplit(tiles, (long long)nseg * nk);
+    return acc_ksplit(tiles, (long long)nseg * nk);
   };
   auto run = [&](int cfg, int ksplit) {
     dim3 grid;
@@ -1121,9 +1134,12 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
     }
   }
   if (have) {
-    // a stored K split larger than the reduction allows falls back to the default rule
-    const int ks = (chosen.ksplit > 1 && (long long)chosen.ksplit * 8 > (long long)nseg * nk) ? ks_for(kGemmCfgs[chosen.cfg].bn)
-                                                                                             : chosen.ksplit;
+    // long accumulating reductions always take the K-derived split (the table is keyed by
+    // size classes, and a stored split may come from another K); a stored split larger than
+    // the reduction allows falls back to the rule
+    int ks = chosen.ksplit;
+    if ((long long)nseg * nk > ACC_STEPS || ((long long)ks * 8 > (long long)nseg * nk && ks > 1))
+      ks = ks_for(kGemmCfgs[chosen.cfg].bn);
     run(chosen.cfg, acc ? ks : 1);
     return;
   }
@@ -1145,7 +1161,9 @@ void gemm_bf16(int site, int M, int N, long long K, int nseg, const __nv_bfloat1
   float best_ms = 1e30f;
   for (int cfg = 0; cfg < NGEMMCFG; ++cfg) {
     const int ksd = ks_for(kGemmCfgs[cfg].bn);
-    const int nsplit = (acc && ksd > 1) ? 2 : 1;
+    // long accumulating reductions keep their K-derived split (the summation order must not
+    // depend on the tile choice); short ones may also run unsplit
+    const int nsplit = (acc && ksd > 1 && (long long)nseg * nk <= ACC_STEPS) ? 2 : 1;
     for (int sp = 0; sp < nsplit; ++sp) {
       const int ks = sp == 0 ? ksd : 1;
       float t = 1e30f;
