@@ -207,7 +207,7 @@ def run_ours(args, world, rank, local):
     o, v, Q = w["nocc"], w["nvir"], w["naux"]
     inp = make_dot_inputs(w)
     # the large dot holds about 90 GB of integrals and their copies; 140 GB of sigma workspace
-    # (14 half-vectors per chunk) fit beside them
+    # (about 10 half-vectors per chunk at 14 GB each) fit beside them
     ws = args.workspace_gb if args.workspace_gb > 0 else w.get("workspace_gb", 0.0)
     opt_kw = dict(prec=pp.PP_BF16, order=w["order"], select=0, res_tol=RES_TOL, block=w["block"], refine=1,
                   max_iter=300, cuda_stream=stream.cuda_stream, workspace_gb=ws)
