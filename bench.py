@@ -12,7 +12,10 @@ residual of 1e-6).  --workload batched-128x512x1536 runs the 8-window x k = 8 ba
 
 A step is one block iteration of the window batch: the whole hot path once -- Rayleigh-Ritz
 and the folded extraction, residuals, weighted-Jacobi directions, block CGS2, and one sigma
-batch per precision phase of every window's new vectors (pp_windows_step).  value =
+batch per precision phase of every window's new vectors (pp_windows_step).  On the large dot
+the batch is one window, and the four windows are solved in turn (each starts when the one
+before it finishes): a block iteration of one window there takes about 12 s in the BF16
+phase and 36 s in the split phase.  value =
 algorithmic sigma TFLOP/s of the timed steps (each contraction counted once; the split form's
 three products count as one).  With --full-solve (the default for the two smaller workloads)
 the solve continues after the timed steps and its converged roots per second are reported
@@ -48,10 +51,13 @@ WORKLOADS = {
     # one window, k = 8 (the plain-vs-mixed comparison)
     "dot-64x256x768": dict(nocc=64, nvir=256, naux=768, seed=1, mode="perturbative", pct=20.0, nwin=1, delta=0.1,
                            k=8, block=8, order=2, full_solve=True),
-    # 4 windows x k = 16 (the large dot: a block iteration takes about 50 s, a full solve tens of
-    # minutes, so the solve is not finished by default)
+    # 4 windows x k = 16, solved one window at a time (the large dot: a block iteration of one
+    # window takes about 12 s in the BF16 phase and 36 s in the split phase, a window's solve
+    # tens of minutes, so it is not finished by default; the four windows batched together
+    # would make one split-phase step about 145 s)
     "dot-256x1024x3072": dict(nocc=256, nvir=1024, naux=3072, seed=4, mode="perturbative", pct=20.0, nwin=4,
-                              delta=0.05, k=16, block=16, order=2, full_solve=False, workspace_gb=140.0),
+                              delta=0.05, k=16, block=16, order=2, full_solve=False, workspace_gb=140.0,
+                              in_turn=True),
 }
 DEFAULT_WORKLOAD = "dot-256x1024x3072"
 METRIC = "converged roots/s & sigma TFLOP/s at <=1e-6 Ha vs FP64 oracle; p50/p99 window latency"
@@ -163,6 +169,17 @@ def windows_for_rank(omega0: float, delta: float, nwin: int, rank: int):
     return [window_for_rank(omega0, delta, rank * nwin + w) for w in range(nwin)]
 
 
+def window_batches(w):
+    """Which windows are stepped together: all of them in one batch, or (workloads with
+    in_turn) one window at a time, the windows taken in turn as each one finishes."""
+    n = w["nwin"]
+    return [[i] for i in range(n)] if w.get("in_turn") else [list(range(n))]
+
+
+def next_batch(b: int, nbatches: int) -> int:
+    return (b + 1) % nbatches
+
+
 def make_dot_inputs(w, b_dtype=np.float32):
     from synth.inputs import make_inputs
 
@@ -221,15 +238,22 @@ def run_ours(args, world, rank, local):
     deltas = [w["delta"]] * w["nwin"]
     ks = [w["k"]] * w["nwin"]
 
-    # ---- the batched solve, one block iteration per step --------------------------------
+    # ---- the solve, one block iteration per step ------------------------------------------
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    run = dot.windows(wins, deltas, ks)
+    batches = window_batches(w)
+    bidx = 0
+
+    def start(b):
+        sel = batches[b]
+        return dot.windows([wins[i] for i in sel], [deltas[i] for i in sel], [ks[i] for i in sel])
+
+    run = start(0)
     solves = []  # (roots converged, ms, iterations, sigma supervectors, max resid) per completed batch
     cur = dict(ms=0.0, it=0, nv=0)
 
     def one_step():
-        nonlocal run
+        nonlocal run, bidx
         ev0.record(stream)
         un, nv, nc = run.step()
         ev1.record(stream)
@@ -238,14 +262,15 @@ def run_ours(args, world, rank, local):
         cur["ms"] += ms
         cur["it"] += 1
         cur["nv"] += nv
-        if un == 0:  # the batch is done: collect it and start the same windows again
+        if un == 0:  # the batch is done: collect it and start the next one (or the same again)
             res, st = run.end(allow_notconv=True)
             roots = sum(int(np.count_nonzero(r["resid"] <= RES_TOL * 1.0000001)) for r in res)
             mres = max((float(r["resid"].max()) for r in res if len(r["resid"])), default=None)
             solves.append(dict(roots=roots, ms=cur["ms"], iterations=cur["it"], sigma_vectors=cur["nv"],
                                max_resid=mres, status=int(st), found=[len(r["omega"]) for r in res]))
             cur.update(ms=0.0, it=0, nv=0)
-            run = dot.windows(wins, deltas, ks)
+            bidx = next_batch(bidx, len(batches))
+            run = start(bidx)
         return ms, step_flops(o, v, Q, nv, nc), nv
 
     for _ in range(max(args.warmup, 0)):
@@ -338,7 +363,10 @@ def run_ours(args, world, rank, local):
         config=dict(workload=args.workload, nocc=o, nvir=v, naux=Q, windows=w["nwin"], k=w["k"],
                     window_ha=w["delta"], block=w["block"], order=w["order"],
                     precision="bf16 tensor cores + fp64 krylov + bf16x3 refinement to 1e-6",
-                    inputs=w["mode"], step="one block iteration of all windows (pp_windows_step)",
+                    inputs=w["mode"],
+                    step=("one block iteration of the current window (pp_windows_step on a one-window batch; "
+                          "the windows solved in turn)") if w.get("in_turn") else
+                         "one block iteration of all windows (pp_windows_step)",
                     l2="inputs larger than L2 (FP32 B tensor %.1f GB; slab and operands > 129 MB)" % (inp.B.nbytes / 1e9),
                     parallelism=f"replicas{world}"),
         roots=roots_obj,

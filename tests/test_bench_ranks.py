@@ -50,3 +50,20 @@ def test_rank_windows_are_disjoint_and_flop_model():
     assert ladder < per_vec < 1.05 * ladder
     assert bench.tgen_flops(o, v, Q) == 2.0 * Q * (o * v) ** 2
     assert bench.step_flops(o, v, Q, 10, 2) == 10 * per_vec + 2 * bench.tgen_flops(o, v, Q)
+
+
+def test_window_batches_in_turn_and_together():
+    import bench
+
+    big = bench.WORKLOADS["dot-256x1024x3072"]
+    assert bench.window_batches(big) == [[0], [1], [2], [3]]
+    batched = bench.WORKLOADS["batched-128x512x1536"]
+    assert bench.window_batches(batched) == [list(range(8))]
+    # windows taken in turn, wrapping round; one batch restarts itself
+    seq, b = [], 0
+    for _ in range(6):
+        seq.append(b)
+        b = bench.next_batch(b, 4)
+    assert seq == [0, 1, 2, 3, 0, 1]
+    assert bench.next_batch(0, 1) == 0
+    assert bench.DEFAULT_WORKLOAD == "dot-256x1024x3072" and not big["full_solve"]
