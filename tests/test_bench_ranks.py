@@ -67,3 +67,24 @@ def test_window_batches_in_turn_and_together():
     assert seq == [0, 1, 2, 3, 0, 1]
     assert bench.next_batch(0, 1) == 0
     assert bench.DEFAULT_WORKLOAD == "dot-256x1024x3072" and not big["full_solve"]
+
+
+def test_reference_arm_line_shape():
+    """The reference arm (the oracle on the host cores) prints the contract's line: same metric,
+    unit and config as the GPU arm, impl reference, its own cpu_baseline and an e2e with no
+    copies; ranks other than 0 do no work."""
+    import argparse
+    import json
+
+    import bench
+
+    args = argparse.Namespace(workload=bench.DEFAULT_WORKLOAD, steps=1, warmup=0)
+    assert bench.run_reference(args, 2, 1) is None
+    line = bench.run_reference(args, 1, 0)
+    json.dumps(line)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "TFLOP/s"
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["value"] > 0
+    assert line["config"]["workload"] == bench.DEFAULT_WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == dict(value=line["value"], unit="TFLOP/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
